@@ -1,0 +1,193 @@
+/*
+ * qap_pso.h -- C-ABI of the GB300 multi-swarm PSO for the Quadratic Assignment
+ * Problem (Szwed & Chmiel, "Multi-swarm PSO algorithm for the Quadratic
+ * Assignment Problem: a massive parallel implementation on the OpenCL
+ * platform", arXiv 1504.05158).
+ *
+ * Problem (section 2.1, Eq. 1 and Eq. 2): facilities 0..n-1 with flows F[i][j],
+ * locations 0..n-1 with distances D[k][l]; an assignment p places facility i at
+ * location p[i] and costs f(p) = sum_i sum_j F[i][j] * D[p[i]][p[j]].
+ *
+ * One PSO iteration (section 3.1 and 3.2) updates every particle of every swarm:
+ *   velocity  V(t+1) = S_v(c1 V(t) + c2 r2 (P^L - X(t)) + c3 r3 (P^G - X(t)))   (Eq. 4)
+ *   position  X(t+1) = S_x(X(t) + V(t))                                        (Eq. 5)
+ *             with S_x = SecondTarget (Algorithm 1; depth 0 = GlobalMax),
+ *   then the goal function, a best-improvement swap local search, the local
+ *   best P^L, the swarm bests P^G and the migration between swarms (Algorithm 2,
+ *   or a ring). Every random draw is Philox4x32-10 keyed by the seed and
+ *   counted by (particle in swarm, swarm, iteration, purpose).
+ *
+ * Conventions for every function:
+ *   - return a status code (QAP_OK = 0 or one of QAP_ERR_*); never abort;
+ *   - output arguments are left untouched when the status is not QAP_OK;
+ *   - matrices are row-major n x n int32; permutations are int32 arrays of n
+ *     entries, 0-based, facility -> location;
+ *   - pointers are host pointers unless the comment says "device";
+ *   - handles own the device memory they allocate; the caller keeps ownership of
+ *     every buffer it passes in;
+ *   - a state is used by one host thread at a time; its work is queued on its
+ *     CUDA stream; functions that return results to the host synchronise that
+ *     stream.
+ */
+#ifndef QAP_PSO_H
+#define QAP_PSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define QAP_OK 0
+#define QAP_ERR_INVALID_ARG 1 /* a size, pointer or parameter is out of range */
+#define QAP_ERR_OOM 2         /* device memory could not be allocated */
+#define QAP_ERR_CUDA 3        /* a CUDA call or kernel failed */
+#define QAP_ERR_TIMEOUT 4     /* a bounded device wait gave up */
+#define QAP_ERR_OVERFLOW 5    /* the instance's values could overflow the exact integer path */
+#define QAP_ERR_UNSUPPORTED 6 /* a valid request this build does not implement */
+
+/* Human-readable name of a status code (static string). */
+const char* qap_status_string(int status);
+
+/* ------------------------------------------------------------- instances */
+typedef struct qap_instance* qap_instance_t;
+
+/* Copies F and D (host, row-major n x n int32, entries >= 0 as section 2.1
+ * requires) to the device. n in [2, 256]. Records whether both matrices are
+ * symmetric with a zero diagonal (the case the GPU local search implements) and
+ * the value bounds that select the exact integer arithmetic. Errors:
+ * QAP_ERR_INVALID_ARG for n out of range, NULL pointers or negative entries;
+ * QAP_ERR_OOM / QAP_ERR_CUDA on device failures. */
+int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_instance_t* out);
+void qap_destroy_instance(qap_instance_t inst);
+
+typedef struct {
+    int32_t n;
+    int32_t symmetric_zero_diag; /* 1 if F and D are both symmetric with zero diagonal */
+    int32_t max_f, max_d;        /* largest entries */
+    int32_t exact_int32;         /* 1 if n * max_f * max_d < 2^27 (all swap values fit int32) */
+} qap_instance_info_t;
+int qap_instance_info(qap_instance_t inst, qap_instance_info_t* out);
+
+/* ------------------------------------------------------------ parameters */
+enum { PSO_SV_RAW = 0, PSO_SV_NORM = 1 };              /* S_v, section 3.1 */
+enum { PSO_SX_ALG1 = 0, PSO_SX_TOPD = 1 };             /* which elements SecondTarget ignores */
+enum { PSO_TIE_RANDOM = 0, PSO_TIE_FIRST = 1 };        /* choice inside the set M of Algorithm 1 */
+enum { PSO_MIG_NONE = 0, PSO_MIG_RANK = 1, PSO_MIG_RING = 2 };
+enum { PSO_V_FP32 = 0, PSO_V_BF16 = 1 };               /* storage of V; arithmetic is fp32 */
+
+typedef struct {
+    int32_t swarms;         /* m >= 1 */
+    int32_t swarm_size;     /* particles per swarm >= 1 */
+    float c1, c2, c3;       /* inertia, self recognition, social factor (Eq. 4) */
+    int32_t sv_kind;        /* PSO_SV_RAW: clamp to [-v_max, v_max]; PSO_SV_NORM: clamp then
+                               divide each column by its L1 norm (section 3.1) */
+    float v_max;            /* > 0 */
+    int32_t sx_rule;        /* PSO_SX_ALG1: Algorithm 1 as printed (all elements of X(t) equal
+                               to 1 ignored in the first `depth` steps); PSO_SX_TOPD: only the
+                               `depth` largest of them (the reading that reproduces Eq. 6) */
+    int32_t depth;          /* SecondTarget depth, 0 <= depth < n; 0 = GlobalMax */
+    int32_t tie_rule;       /* PSO_TIE_RANDOM (Algorithm 1) or PSO_TIE_FIRST */
+    int32_t pos_uses_new_v; /* 0: Eq. 5 literal, X(t) + V(t); 1: X(t) + V(t+1) */
+    int32_t ls_max_moves;   /* swap local search: < 0 none, 0 until no improving swap, > 0 cap */
+    int32_t ls_at_init;     /* 1: also run the local search on the initial particles */
+    int32_t mig_kind;       /* PSO_MIG_* (section 3.2) */
+    int32_t mig_depth;      /* Algorithm 2's d, 0 <= 2 d < m */
+    int32_t mig_period;     /* migrate after every mig_period-th iteration (>= 1) */
+    int32_t ring_if_better; /* ring: replace P^G of swarm k+1 only if strictly better */
+    int32_t v_storage;      /* PSO_V_FP32 or PSO_V_BF16 (round to nearest even) */
+} pso_params_t;
+
+/* Fills the defaults: m = 1, 32 particles, c1 = 0.8, c2 = c3 = 0.5 (the esc32
+ * setting of section 4.1), Norm, v_max = 1, Algorithm 1 with depth 2, random
+ * ties, Eq. 5 literal, local search to a local optimum, no migration, fp32. */
+void pso_params_default(pso_params_t* p);
+
+/* ----------------------------------------------------------------- state */
+typedef struct pso_state* pso_state_t;
+
+/* Allocates the population on the device and initialises it (random particles,
+ * section 3.3): X(0) by a Fisher-Yates shuffle and V(0) uniform in
+ * [-v_max, v_max), both from Philox; cost, P^L = X(0), P^G and the global best.
+ * `stream` is a cudaStream_t (NULL = a new stream owned by the state). The state
+ * keeps a pointer to `inst`, which must outlive it. Errors: QAP_ERR_INVALID_ARG
+ * (bad parameters), QAP_ERR_UNSUPPORTED (local search requested on an instance
+ * that is not symmetric with zero diagonal, or n above the device limit),
+ * QAP_ERR_OVERFLOW (values too large for the exact int32 path), QAP_ERR_OOM,
+ * QAP_ERR_CUDA. */
+int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, void* stream,
+             pso_state_t* out);
+
+/* Queues `iterations` (>= 0) full iterations on the state's stream and returns
+ * without waiting. Iterations are replayed from a captured CUDA graph. */
+int pso_step(pso_state_t st, int32_t iterations);
+
+/* Best solution found so far (synchronises): its cost, its permutation (n
+ * entries, may be NULL) and the number of completed iterations when it was found
+ * (0 = during initialisation). */
+int pso_best(pso_state_t st, int64_t* cost, int32_t* perm, int32_t* iter_found);
+
+typedef struct {
+    uint32_t size;          /* caller sets sizeof(pso_stats_t) */
+    int32_t iteration;      /* completed iterations */
+    int64_t best_cost;      /* global best ever */
+    int64_t min, p5, p25, p50, p75, max; /* current costs, nearest-rank percentiles
+                                            (section 4.2) */
+    double mean;
+    int64_t particle_iterations; /* counters since pso_init */
+    int64_t ls_moves, ls_rounds;
+    int64_t delta_full;     /* swap values formed from a fresh O(n^3) set-up (first round) */
+    int64_t delta_incr;     /* swap values formed after an O(n^2) rank-1 update */
+    int64_t sx_ties;        /* S_x steps whose set M had more than one element */
+} pso_stats_t;
+
+/* Population statistics of the current costs plus counters (synchronises). */
+int pso_stats(pso_state_t st, pso_stats_t* out);
+
+void pso_destroy(pso_state_t st);
+
+/* ------------------------------------------------ state export / import */
+/* Host copies of the whole state, e.g. for checkpoints and for comparing one
+ * iteration with an independent implementation. Sizes: P = swarms * swarm_size.
+ * V is exported as fp32 values (exact for bf16 storage). */
+typedef struct {
+    float* V;        /* P * n * n, row = location, column = facility */
+    int32_t* X;      /* P * n current positions */
+    int32_t* X_sx;   /* P * n S_x results of the last iteration, before local search */
+    int32_t* PL;     /* P * n */
+    int64_t* costL;  /* P */
+    int64_t* cost;   /* P */
+    int32_t* moves;  /* P local-search moves of the last iteration */
+    int32_t* PG;     /* swarms * n */
+    int64_t* costG;  /* swarms */
+    int32_t* best;   /* n */
+    int64_t best_cost;
+    int32_t best_iter;
+    int32_t t;       /* completed iterations */
+} pso_host_state_t;
+
+/* Copies the device state into caller-owned host buffers (synchronises). */
+int pso_export_state(pso_state_t st, pso_host_state_t* out);
+/* Overwrites the device state from host buffers (V values are rounded to the
+ * storage format; X_sx and moves are ignored). Synchronises. */
+int pso_import_state(pso_state_t st, const pso_host_state_t* in);
+
+/* ------------------------------------------------ single-kernel entry points */
+/* Goal function (Eq. 1) of `count` permutations (host, count x n int32) on the
+ * device; out: count int64. */
+int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int64_t* out);
+
+/* Best-improvement swap local search (the search of every iteration) on `count`
+ * permutations (host, count x n int32, improved in place), max_moves as
+ * pso_params_t.ls_max_moves (>= 0). Outputs (host, count entries each, any may be
+ * NULL): final costs, moves, rounds (neighbourhood evaluations). Requires a
+ * symmetric zero-diagonal instance. */
+int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
+                     int64_t* costs, int32_t* moves, int32_t* rounds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput of the multi-swarm PSO iteration for the QAP on one GB300 per rank.
+
+Workload (the paper-shaped n = 64 case): D = Manhattan distances on an 8 x 8 grid,
+F symmetric with 30 % log-uniform flows in [1, 99]; 16 swarms x 640 particles
+(10 240), ring migration of each swarm's best every 20 iterations, full swap local
+search, SecondTarget depth 2, Norm velocities. A step is one iteration over every
+particle. Inputs are synthetic (QAPLIB is not available).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). The reference arm times the plain CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-iterations/s and swap-Δ evals/s on 1 GB300, n=64, 10k particles"
+UNIT = "particle-iterations/s"
+N, SWARMS, SWARM_SIZE, RING_PERIOD = 64, 16, 640, 20
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload_config(storage="fp32"):
+    return {"workload": "grid64: n=64 8x8-grid Manhattan D, 30% log-uniform F; 16 swarms x 640 "
+                        "particles, ring migration every 20 iterations, full swap local search",
+            "n": N, "swarms": SWARMS, "swarm_size": SWARM_SIZE, "particles": SWARMS * SWARM_SIZE,
+            "v_storage": storage, "sx": "SecondTarget depth 2 (Algorithm 1)", "sv": "Norm",
+            "c": [0.8, 0.5, 0.5], "l2": "flushed before every timed iteration (256 MiB write)"}
+
+
+def params(Q, storage):
+    return Q.default_params(swarms=SWARMS, swarm_size=SWARM_SIZE, mig_kind=Q.MIG_RING,
+                            mig_period=RING_PERIOD, v_storage=storage, depth=2, sv_kind=Q.SV_NORM)
+
+
+# ----------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", self.gpu, "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- our arm
+
+def algorithmic(n, dmoves, drounds, particles, storage_bytes):
+    """Work of one iteration (see the roofline notes of the design document)."""
+    npairs = n * (n - 1) // 2
+    k1_bytes = particles * (2 * n * n * storage_bytes + 3 * n)
+    k2_ops = particles * 2 * n ** 3 + drounds * npairs * 10 + dmoves * 2 * n * n
+    return k1_bytes, k2_ops
+
+
+def measure(Q, W, torch, storage, steps, warmup, rank, flush):
+    inst = W.grid64()
+    gi = Q.Instance(inst.F, inst.D)
+    stream = torch.cuda.Stream()
+    prm = params(Q, storage)
+    sw = Q.Swarm(gi, prm, seed=64 + rank, stream=stream.cuda_stream)
+    sw.step(warmup)
+    torch.cuda.synchronize()
+    s0 = sw.stats()
+    return sw, s0, stream
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1504_05158_gb300 import build as B
+    B.build()
+    from paper_1504_05158_gb300 import qap_pso as Q
+    from paper_1504_05158_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak_tops = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # int32 lanes x (mul + add) x clock
+
+    results = {}
+    for storage_name, storage in (("fp32", Q.V_FP32), ("bf16", Q.V_BF16)):
+        sw, s0, stream = measure(Q, W, torch, storage, args.steps, args.warmup, rank, flush)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device() if world == 1 else local_rank) as clk:
+            ms = sw.step_timed(args.steps, flush.data_ptr(), flush.numel())
+        torch.cuda.synchronize()
+        barrier()
+        s1 = sw.stats()
+        span = ms[3] / 1e3
+        if dist:
+            t = torch.tensor([span], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            span = float(t.item())
+        pits = SWARMS * SWARM_SIZE * args.steps * world
+        dfull = s1["delta_full"] - s0["delta_full"]
+        dincr = s1["delta_incr"] - s0["delta_incr"]
+        dmoves = s1["ls_moves"] - s0["ls_moves"]
+        drounds = s1["ls_rounds"] - s0["ls_rounds"]
+        k1_bytes, k2_ops = algorithmic(N, dmoves / args.steps, drounds / args.steps,
+                                       SWARMS * SWARM_SIZE, 4 if storage == Q.V_FP32 else 2)
+        k1_ms, k2_ms, k3_ms = (m / args.steps for m in ms[:3])
+        best, _, best_it = sw.best()
+        results[storage_name] = dict(
+            value=pits / span, ms_per_step=span * 1e3 / args.steps,
+            delta_evals_per_s=(dfull + dincr) * world / span,
+            delta_full_per_s=dfull * world / span, delta_incr_per_s=dincr * world / span,
+            kernel_ms={"velocity_sx": k1_ms, "cost_ls": k2_ms, "bests_migration": k3_ms},
+            k1_gbs=k1_bytes / (k1_ms / 1e3) / 1e9, k2_tops=k2_ops / (k2_ms / 1e3) / 1e12,
+            k1_bytes=k1_bytes, k2_ops=k2_ops,
+            moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * args.steps),
+            best_cost=best, best_iter=best_it, iterations=args.warmup + args.steps,
+            clocks=clk.summary())
+        sw.close()
+
+    # end to end through the C-ABI with host buffers: instance upload, init, K iterations
+    # each followed by a read-back of the best cost and permutation
+    inst = W.grid64()
+    F = torch.from_numpy(inst.F).pin_memory()
+    D = torch.from_numpy(inst.D).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    gi = Q.Instance(F.numpy(), D.numpy())
+    sw = Q.Swarm(gi, params(Q, Q.V_FP32), seed=640 + rank)
+    for _ in range(args.steps):
+        sw.step(1)
+        sw.best()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    sw.close()
+    gi.close()
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": SWARMS * SWARM_SIZE * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * N * N * 4 / args.steps,
+           "d2h_bytes_per_step": 8 + 4 + N,
+           "what": "qap_create_instance + pso_init + K x (pso_step(1) + pso_best), host F and D"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        r = results["fp32"]
+        k1, k2 = r["kernel_ms"]["velocity_sx"], r["kernel_ms"]["cost_ls"]
+        if k2 >= k1:
+            roof = {"kernel": "k_ls (goal function + swap local search)", "bound": "alu",
+                    "achieved": r["k2_tops"], "peak": alu_peak_tops, "unit": "Tops/s",
+                    "frac": r["k2_tops"] / alu_peak_tops, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"}
+        else:
+            roof = {"kernel": "k_velocity_sx", "bound": "hbm", "achieved": r["k1_gbs"],
+                    "peak": hbm_peak, "unit": "GB/s", "frac": r["k1_gbs"] / hbm_peak,
+                    "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config("fp32"),
+            "delta_evals_per_s": r["delta_evals_per_s"],
+            "delta_full_per_s": r["delta_full_per_s"], "delta_incr_per_s": r["delta_incr_per_s"],
+            "kernel_ms_per_step": r["kernel_ms"],
+            "hbm_velocity_sx": {"achieved_gbs": r["k1_gbs"], "peak_gbs": hbm_peak,
+                                "frac": r["k1_gbs"] / hbm_peak},
+            "alu_cost_ls": {"achieved_tops": r["k2_tops"], "peak_tops": alu_peak_tops,
+                            "frac": r["k2_tops"] / alu_peak_tops},
+            "roofline": roof,
+            "bf16": {k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
+                                                      "kernel_ms", "k1_gbs", "best_cost")},
+            "quality": {"fp32_best": r["best_cost"], "bf16_best": results["bf16"]["best_cost"],
+                        "bf16_vs_fp32": results["bf16"]["best_cost"] / r["best_cost"] - 1.0,
+                        "iterations": r["iterations"]},
+            "moves_per_particle_iteration": r["moves_per_pit"],
+            "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": r["clocks"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------- oracle
+
+def oracle_sample(steps, warmup, budget_s=None):
+    """The plain oracle on a bounded sample of the workload: 2 swarms x 32 particles of
+    the same instance and parameters, `warmup` untimed then `steps` timed iterations."""
+    from oracle import oracle as O
+    from paper_1504_05158_gb300 import workloads as W
+    inst = W.grid64()
+    q = O.make_params(swarms=2, swarm_size=32, mig_kind=2, mig_period=RING_PERIOD, depth=2)
+    s = O.init(q, inst.F, inst.D, 64)
+    O.step(q, inst.F, inst.D, 64, s, warmup)
+    c0 = s.counters.copy()
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        O.step(q, inst.F, inst.D, 64, s, 1)
+        done += 1
+        if budget_s and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    c1 = s.counters
+    pit = int(c1[O.C_PIT] - c0[O.C_PIT])
+    dev = int(c1[O.C_DELTA_FULL] + c1[O.C_DELTA_INCR] - c0[O.C_DELTA_FULL] - c0[O.C_DELTA_INCR])
+    return {"value": pit / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "delta_evals_per_s": dev / dt,
+            "sample": f"2 swarms x 32 particles of the same n=64 instance, {done} timed "
+                      f"iterations after {warmup} warm-up, single thread"}
+
+
+def cpu_baseline(args):
+    return oracle_sample(steps=40, warmup=3, budget_s=15.0)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    r = oracle_sample(steps=args.steps, warmup=args.warmup, budget_s=120.0)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * 64 / r["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config("fp64 (oracle)"), "impl": "reference",
+            "cpu_baseline": {k: r[k] for k in ("kind", "cores", "sample", "value", "unit")},
+            "delta_evals_per_s": r["delta_evals_per_s"],
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,16 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
  * without waiting. Iterations are replayed from a captured CUDA graph. */
 int pso_step(pso_state_t st, int32_t iterations);
 
+/* Like pso_step, but launches each kernel of every iteration directly (no graph)
+ * with CUDA events around it on the state's stream, then synchronises. Adds into
+ * ms_out[0..3] the device milliseconds of (0) velocity + S_x, (1) goal function +
+ * local search, (2) bests + migration, summed over the iterations, and (3) the sum
+ * of each iteration's span from its first kernel's start to its last kernel's end.
+ * If flush_buf (device, flush_bytes long) is not NULL it is overwritten before every
+ * iteration, outside the timed spans, to evict the L2 cache. For measurement. */
+int pso_step_timed(pso_state_t st, int32_t iterations, void* flush_buf, size_t flush_bytes,
+                   float* ms_out);
+
 /* Best solution found so far (synchronises): its cost, its permutation (n
  * entries, may be NULL) and the number of completed iterations when it was found
  * (0 = during initialisation). */
@@ -141,6 +151,7 @@ typedef struct {
     int64_t delta_full;     /* swap values formed from a fresh O(n^3) set-up (first round) */
     int64_t delta_incr;     /* swap values formed after an O(n^2) rank-1 update */
     int64_t sx_ties;        /* S_x steps whose set M had more than one element */
+    int64_t errors;         /* internal consistency failures detected by the kernels (0) */
 } pso_stats_t;
 
 /* Population statistics of the current costs plus counters (synchronises). */

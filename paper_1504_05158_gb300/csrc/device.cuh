@@ -1,0 +1,117 @@
+// Device-side building blocks shared by the kernels of the PSO iteration:
+// the Philox4x32-10 counter-based generator, the float ordering key used by the
+// S_x argmax, storage-format conversions, and the device view of a state.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace qap {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// ----------------------------------------------------------------------- RNG
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round takes
+// the 64-bit products of words 0 and 2 with two odd constants, mixes their high
+// halves with words 1 and 3 and the round key, and advances the key by two Weyl
+// increments. key = (seed low, seed high); counter = (c0, c1, c2, tag<<24 | block).
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                      uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+enum : uint32_t { TAG_R = 0, TAG_TIE = 1, TAG_INIT_X = 2, TAG_INIT_V = 3, TAG_MIG = 4 };
+
+__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                                    uint32_t tag, uint32_t block) {
+    return philox(c0, c1, c2, (tag << 24) | (block & 0xFFFFFFu), (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t word_of(const U4& u, int i) {
+    return i == 0 ? u.x : (i == 1 ? u.y : (i == 2 ? u.z : u.w));
+}
+
+// top 24 bits as a fraction in [0, 1); exact in fp32
+__device__ __forceinline__ float u01f(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
+// floor(u * k / 2^32) in [0, k)
+__device__ __forceinline__ uint32_t below(uint32_t u, uint32_t k) {
+    return (uint32_t)(((uint64_t)u * (uint64_t)k) >> 32);
+}
+
+// --------------------------------------------------------------- float keys
+// Monotone map float -> uint32 (larger float, larger key); +0 and -0 share a key;
+// no finite float maps to 0, which marks "nothing".
+__device__ __forceinline__ uint32_t fkey(float f) {
+    uint32_t b = __float_as_uint(f == 0.0f ? 0.0f : f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// ---------------------------------------------------------- storage formats
+template <typename VT>
+struct VStore;
+template <>
+struct VStore<float> {
+    static __device__ __forceinline__ float load(const float* p) { return *p; }
+    static __device__ __forceinline__ float to_f(float v) { return v; }
+    static __device__ __forceinline__ float from_f(float v) { return v; }
+};
+template <>
+struct VStore<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------------ device state
+// Everything one iteration touches, by value in each kernel's arguments. Pointers
+// never change after pso_init, so captured graphs stay valid.
+struct StateView {
+    int32_t n, m, ss, P;
+    int32_t ps;       // bytes between consecutive permutations (>= n, multiple of 16)
+    int64_t vstride;  // elements between consecutive particles' V tiles (multiple of 8)
+    void* V;          // P tiles of n x n, row = location, column = facility
+    uint8_t* X;       // current positions
+    uint8_t* Xsx;     // S_x results of the running iteration
+    uint8_t* PL;
+    int64_t* costL;
+    int64_t* cost;
+    int32_t* moves;   // per particle, last iteration
+    int32_t* rounds;  // per particle, last iteration
+    uint8_t* PG;      // m swarm bests
+    uint8_t* PG2;     // ring snapshot
+    int64_t* costG;
+    int64_t* costG2;
+    uint8_t* best;
+    int64_t* best_cost;
+    int32_t* best_iter;
+    int32_t* t;       // completed iterations (device-resident so graph replays advance it)
+    unsigned long long* counters;
+    uint64_t seed;
+    float c1, c2, c3, v_max;
+    int32_t sv_kind, sx_rule, depth, tie_rule, pos_uses_new_v;
+    int32_t ls_max_moves, mig_kind, mig_depth, mig_period, ring_if_better;
+};
+
+// counters[CNT_ERR] counts internal consistency failures (a kernel that detects one
+// skips the access instead of faulting; the host reports it).
+enum { CNT_PIT = 0, CNT_MOVES, CNT_ROUNDS, CNT_DELTA_FULL, CNT_DELTA_INCR, CNT_TIES, CNT_ERR, CNT_N };
+
+}  // namespace qap

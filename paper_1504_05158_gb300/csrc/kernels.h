@@ -1,0 +1,45 @@
+// Host-side launchers of the PSO-iteration kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+
+namespace qap {
+
+// Arguments of the goal-function / local-search kernel. Permutations are uint8
+// rows (facility -> location) `ps_in` / `ps_out` bytes apart.
+struct LsArgs {
+    int32_t n, count;
+    int32_t ps_in, ps_out;
+    const int32_t* F;  // device n x n, symmetric with zero diagonal when max_moves >= 0
+    const int32_t* D;  // device n x n
+    const uint8_t* in;
+    uint8_t* out;
+    int64_t* cost;     // count
+    int32_t* moves;    // count, may be null
+    int32_t* rounds;   // count, may be null
+    uint8_t* PL;       // local bests to update (may be null)
+    int64_t* costL;
+    unsigned long long* counters;  // may be null
+    int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
+};
+
+// Largest n the local search supports (one warp's G matrix in shared memory).
+int ls_max_n();
+cudaError_t launch_ls(const LsArgs& a, cudaStream_t st);
+
+cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st);
+cudaError_t launch_velocity_sx(const StateView& s, int v_bf16, cudaStream_t st);
+int velocity_sx_max_n(int v_bf16);
+// init_mode: the bookkeeping after initialisation (no migration, t unchanged).
+cudaError_t launch_bests(const StateView& s, int init_mode, cudaStream_t st);
+int bests_max_swarms();
+
+// Sorts `count` costs in `scratch` (>= next power of two entries) and writes
+// {min, p5, p25, p50, p75, max} to out6 and the mean to *mean (device pointers).
+cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, int32_t scratch_len,
+                         int64_t* out6, double* mean, cudaStream_t st);
+
+}  // namespace qap

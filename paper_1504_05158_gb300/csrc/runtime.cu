@@ -1,0 +1,654 @@
+// C-ABI of the library (declared in include/qap_pso.h): instances, population
+// state, the iteration loop as a captured CUDA graph, results, statistics,
+// state export/import and the single-kernel entry points.
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/qap_pso.h"
+#include "kernels.h"
+
+using namespace qap;
+
+struct qap_instance {
+    int32_t n;
+    int32_t* dF;
+    int32_t* dD;
+    int32_t sym_zd;
+    int32_t max_f, max_d;
+    int32_t exact32;
+    int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
+};
+
+struct pso_state {
+    qap_instance* inst;
+    pso_params_t prm;
+    uint64_t seed;
+    cudaStream_t stream;
+    bool own_stream;
+    StateView sv;
+    void* dbase;
+    int64_t* stats_buf;
+    int32_t stats_len;
+    int64_t* stats_out;  // 6 int64 + 1 double
+    cudaGraphExec_t g1, g16;
+};
+
+namespace {
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return QAP_OK;
+    if (e == cudaErrorMemoryAllocation) return QAP_ERR_OOM;
+    return QAP_ERR_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// host round-to-nearest-even float -> bfloat16 bits (finite inputs)
+uint16_t host_bf16(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    if ((b & 0x7F800000u) == 0x7F800000u) return (uint16_t)(b >> 16);  // inf / nan kept
+    const uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7FFFu + lsb;
+    return (uint16_t)(b >> 16);
+}
+float host_from_bf16(uint16_t h) {
+    uint32_t b = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+int validate(const qap_instance* inst, const pso_params_t* p) {
+    const int n = inst->n;
+    if (p->swarms < 1 || p->swarms > bests_max_swarms()) return QAP_ERR_INVALID_ARG;
+    if (p->swarm_size < 1) return QAP_ERR_INVALID_ARG;
+    if ((long long)p->swarms * p->swarm_size > (1LL << 26)) return QAP_ERR_INVALID_ARG;
+    if (!(p->v_max > 0.0f)) return QAP_ERR_INVALID_ARG;
+    if (p->sv_kind != PSO_SV_RAW && p->sv_kind != PSO_SV_NORM) return QAP_ERR_INVALID_ARG;
+    if (p->sx_rule != PSO_SX_ALG1 && p->sx_rule != PSO_SX_TOPD) return QAP_ERR_INVALID_ARG;
+    if (p->depth < 0 || p->depth >= n) return QAP_ERR_INVALID_ARG;  // d < n (section 3.1)
+    if (p->tie_rule != PSO_TIE_RANDOM && p->tie_rule != PSO_TIE_FIRST) return QAP_ERR_INVALID_ARG;
+    if (p->mig_kind < PSO_MIG_NONE || p->mig_kind > PSO_MIG_RING) return QAP_ERR_INVALID_ARG;
+    if (p->mig_depth < 0 || 2 * p->mig_depth >= p->swarms + (p->mig_kind == PSO_MIG_RANK ? 0 : 1 << 30))
+        return QAP_ERR_INVALID_ARG;  // d < m / 2 (Algorithm 2)
+    if (p->mig_period < 1) return QAP_ERR_INVALID_ARG;
+    if (p->v_storage != PSO_V_FP32 && p->v_storage != PSO_V_BF16) return QAP_ERR_INVALID_ARG;
+    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
+    if ((p->ls_max_moves >= 0) && !inst->sym_zd) return QAP_ERR_UNSUPPORTED;
+    if (n > ls_max_n() || n > velocity_sx_max_n(p->v_storage)) return QAP_ERR_UNSUPPORTED;
+    return QAP_OK;
+}
+
+LsArgs ls_args_for(const pso_state* s, bool init) {
+    LsArgs a{};
+    a.n = s->sv.n;
+    a.count = s->sv.P;
+    a.ps_in = a.ps_out = s->sv.ps;
+    a.F = s->inst->dF;
+    a.D = s->inst->dD;
+    a.in = s->sv.Xsx;
+    a.out = s->sv.X;
+    a.cost = s->sv.cost;
+    a.moves = s->sv.moves;
+    a.rounds = s->sv.rounds;
+    a.PL = s->sv.PL;
+    a.costL = s->sv.costL;
+    a.counters = init ? nullptr : s->sv.counters;
+    a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
+    return a;
+}
+
+cudaError_t enqueue_iteration(pso_state* s) {
+    const int bf = s->prm.v_storage == PSO_V_BF16;
+    cudaError_t e = launch_velocity_sx(s->sv, bf, s->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_ls(ls_args_for(s, false), s->stream);
+    if (e != cudaSuccess) return e;
+    return launch_bests(s->sv, 0, s->stream);
+}
+
+cudaError_t capture(pso_state* s, int iters, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < iters; ++i) {
+        e = enqueue_iteration(s);
+        if (e != cudaSuccess) break;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qap_status_string(int status) {
+    switch (status) {
+        case QAP_OK: return "ok";
+        case QAP_ERR_INVALID_ARG: return "invalid argument";
+        case QAP_ERR_OOM: return "out of device memory";
+        case QAP_ERR_CUDA: return "CUDA error";
+        case QAP_ERR_TIMEOUT: return "device wait timed out";
+        case QAP_ERR_OVERFLOW: return "instance values exceed the exact integer path";
+        case QAP_ERR_UNSUPPORTED: return "unsupported by this build";
+        default: return "unknown status";
+    }
+}
+
+int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_instance_t* out) {
+    if (!out || !F || !D || n < 2 || n > 256) return QAP_ERR_INVALID_ARG;
+    int32_t mf = 0, md = 0;
+    int sym = 1;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const int32_t f = F[i * n + j], d = D[i * n + j];
+            if (f < 0 || d < 0) return QAP_ERR_INVALID_ARG;  // non-negative (section 2.1)
+            if (f > mf) mf = f;
+            if (d > md) md = d;
+            if (f != F[j * n + i] || d != D[j * n + i]) sym = 0;
+            if (i == j && (f != 0 || d != 0)) sym = 0;
+        }
+    qap_instance* q = new (std::nothrow) qap_instance();
+    if (!q) return QAP_ERR_OOM;
+    q->n = n;
+    q->sym_zd = sym;
+    q->max_f = mf;
+    q->max_d = md;
+    q->exact32 = ((long double)n * mf * md < (long double)(1 << 27)) ? 1 : 0;
+    q->narrow_ok = md <= 65535 ? 1 : 0;
+    const size_t bytes = (size_t)n * n * 4;
+    cudaError_t e = cudaMalloc(&q->dF, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&q->dD, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(q->dF, F, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(q->dD, D, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(q->dF);
+        cudaFree(q->dD);
+        delete q;
+        return status_of(e);
+    }
+    *out = q;
+    return QAP_OK;
+}
+
+void qap_destroy_instance(qap_instance_t inst) {
+    if (!inst) return;
+    cudaFree(inst->dF);
+    cudaFree(inst->dD);
+    delete inst;
+}
+
+int qap_instance_info(qap_instance_t inst, qap_instance_info_t* out) {
+    if (!inst || !out) return QAP_ERR_INVALID_ARG;
+    out->n = inst->n;
+    out->symmetric_zero_diag = inst->sym_zd;
+    out->max_f = inst->max_f;
+    out->max_d = inst->max_d;
+    out->exact_int32 = inst->exact32;
+    return QAP_OK;
+}
+
+void pso_params_default(pso_params_t* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->swarms = 1;
+    p->swarm_size = 32;
+    p->c1 = 0.8f;
+    p->c2 = 0.5f;
+    p->c3 = 0.5f;
+    p->sv_kind = PSO_SV_NORM;
+    p->v_max = 1.0f;
+    p->sx_rule = PSO_SX_ALG1;
+    p->depth = 2;
+    p->tie_rule = PSO_TIE_RANDOM;
+    p->pos_uses_new_v = 0;
+    p->ls_max_moves = 0;
+    p->ls_at_init = 0;
+    p->mig_kind = PSO_MIG_NONE;
+    p->mig_depth = 0;
+    p->mig_period = 1;
+    p->ring_if_better = 0;
+    p->v_storage = PSO_V_FP32;
+}
+
+int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, void* stream,
+             pso_state_t* out) {
+    if (!inst || !params || !out) return QAP_ERR_INVALID_ARG;
+    int v = validate(inst, params);
+    if (v != QAP_OK) return v;
+    pso_state* s = new (std::nothrow) pso_state();
+    if (!s) return QAP_ERR_OOM;
+    s->inst = inst;
+    s->prm = *params;
+    s->seed = seed;
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+        s->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return status_of(e);
+        }
+        s->own_stream = true;
+    }
+    const int n = inst->n, m = params->swarms, ss = params->swarm_size;
+    const int P = m * ss;
+    StateView& sv = s->sv;
+    sv.n = n;
+    sv.m = m;
+    sv.ss = ss;
+    sv.P = P;
+    sv.ps = (int32_t)align_up(n, 16);
+    sv.vstride = (int64_t)align_up((size_t)n * n, 8);
+    const size_t esz = params->v_storage == PSO_V_BF16 ? 2 : 4;
+    int sl = 1;
+    while (sl < P) sl <<= 1;
+    s->stats_len = sl;
+    // one allocation, 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t oV = take((size_t)P * sv.vstride * esz);
+    const size_t oX = take((size_t)P * sv.ps), oXsx = take((size_t)P * sv.ps), oPL = take((size_t)P * sv.ps);
+    const size_t ocostL = take((size_t)P * 8), ocost = take((size_t)P * 8);
+    const size_t omoves = take((size_t)P * 4), orounds = take((size_t)P * 4);
+    const size_t oPG = take((size_t)m * sv.ps), oPG2 = take((size_t)m * sv.ps);
+    const size_t ocostG = take((size_t)m * 8), ocostG2 = take((size_t)m * 8);
+    const size_t obest = take(sv.ps), obc = take(8), obi = take(4), ot = take(4);
+    const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return status_of(e);
+    }
+    s->dbase = base;
+    sv.V = base + oV;
+    sv.X = (uint8_t*)(base + oX);
+    sv.Xsx = (uint8_t*)(base + oXsx);
+    sv.PL = (uint8_t*)(base + oPL);
+    sv.costL = (int64_t*)(base + ocostL);
+    sv.cost = (int64_t*)(base + ocost);
+    sv.moves = (int32_t*)(base + omoves);
+    sv.rounds = (int32_t*)(base + orounds);
+    sv.PG = (uint8_t*)(base + oPG);
+    sv.PG2 = (uint8_t*)(base + oPG2);
+    sv.costG = (int64_t*)(base + ocostG);
+    sv.costG2 = (int64_t*)(base + ocostG2);
+    sv.best = (uint8_t*)(base + obest);
+    sv.best_cost = (int64_t*)(base + obc);
+    sv.best_iter = (int32_t*)(base + obi);
+    sv.t = (int32_t*)(base + ot);
+    sv.counters = (unsigned long long*)(base + ocnt);
+    s->stats_buf = (int64_t*)(base + ostb);
+    s->stats_out = (int64_t*)(base + osto);
+    sv.seed = seed;
+    sv.c1 = params->c1;
+    sv.c2 = params->c2;
+    sv.c3 = params->c3;
+    sv.v_max = params->v_max;
+    sv.sv_kind = params->sv_kind;
+    sv.sx_rule = params->sx_rule;
+    sv.depth = params->depth;
+    sv.tie_rule = params->tie_rule;
+    sv.pos_uses_new_v = params->pos_uses_new_v;
+    sv.ls_max_moves = params->ls_max_moves;
+    sv.mig_kind = params->mig_kind;
+    sv.mig_depth = params->mig_depth;
+    sv.mig_period = params->mig_period;
+    sv.ring_if_better = params->ring_if_better;
+
+    e = cudaMemsetAsync(base, 0, off, s->stream);
+    if (e == cudaSuccess) e = launch_init(sv, params->v_storage == PSO_V_BF16, s->stream);
+    if (e == cudaSuccess) e = launch_ls(ls_args_for(s, true), s->stream);
+    if (e == cudaSuccess) e = launch_bests(sv, 1, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        pso_destroy(s);
+        return status_of(e);
+    }
+    *out = s;
+    return QAP_OK;
+}
+
+int pso_step(pso_state_t s, int32_t iterations) {
+    if (!s || iterations < 0) return QAP_ERR_INVALID_ARG;
+    if (iterations == 0) return QAP_OK;
+    cudaError_t e = cudaSuccess;
+    if (!s->g1) e = capture(s, 1, &s->g1);
+    if (e == cudaSuccess && iterations >= 16 && !s->g16) e = capture(s, 16, &s->g16);
+    if (e != cudaSuccess) return status_of(e);
+    int left = iterations;
+    while (left >= 16 && e == cudaSuccess) {
+        e = cudaGraphLaunch(s->g16, s->stream);
+        left -= 16;
+    }
+    while (left > 0 && e == cudaSuccess) {
+        e = cudaGraphLaunch(s->g1, s->stream);
+        --left;
+    }
+    return status_of(e);
+}
+
+int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t flush_bytes,
+                   float* ms_out) {
+    if (!s || iterations < 0 || !ms_out) return QAP_ERR_INVALID_ARG;
+    if (iterations == 0) return QAP_OK;
+    std::vector<cudaEvent_t> ev((size_t)iterations * 4, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    const int bf = s->prm.v_storage == PSO_V_BF16;
+    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
+        cudaEvent_t* q = &ev[(size_t)i * 4];
+        if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(q[0], s->stream);
+        if (e == cudaSuccess) e = launch_velocity_sx(s->sv, bf, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(q[1], s->stream);
+        if (e == cudaSuccess) e = launch_ls(ls_args_for(s, false), s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(q[2], s->stream);
+        if (e == cudaSuccess) e = launch_bests(s->sv, 0, s->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(q[3], s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[(size_t)i * 4 + k], ev[(size_t)i * 4 + k + 1]);
+            acc[k] += ms;
+        }
+        float span = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&span, ev[(size_t)i * 4], ev[(size_t)i * 4 + 3]);
+        acc[3] += span;
+    }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return status_of(e);
+    for (int k = 0; k < 4; ++k) ms_out[k] += acc[k];
+    return QAP_OK;
+}
+
+int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
+    if (!s) return QAP_ERR_INVALID_ARG;
+    const int n = s->sv.n;
+    int64_t c = 0;
+    int32_t it = 0;
+    std::vector<uint8_t> p(n);
+    cudaError_t e = cudaMemcpyAsync(&c, s->sv.best_cost, 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&it, s->sv.best_iter, 4, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.data(), s->sv.best, n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return status_of(e);
+    if (cost) *cost = c;
+    if (iter_found) *iter_found = it;
+    if (perm)
+        for (int i = 0; i < n; ++i) perm[i] = p[i];
+    return QAP_OK;
+}
+
+int pso_stats(pso_state_t s, pso_stats_t* out) {
+    if (!s || !out || out->size < sizeof(pso_stats_t)) return QAP_ERR_INVALID_ARG;
+    cudaError_t e = launch_stats(s->sv.cost, s->sv.P, s->stats_buf, s->stats_len, s->stats_out,
+                                 (double*)(s->stats_out + 6), s->stream);
+    int64_t o[7];
+    unsigned long long cnt[CNT_N];
+    int64_t bc = 0;
+    int32_t t = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(o, s->stats_out, 56, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, s->sv.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bc, s->sv.best_cost, 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&t, s->sv.t, 4, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return status_of(e);
+    out->iteration = t;
+    out->best_cost = bc;
+    out->min = o[0];
+    out->p5 = o[1];
+    out->p25 = o[2];
+    out->p50 = o[3];
+    out->p75 = o[4];
+    out->max = o[5];
+    std::memcpy(&out->mean, &o[6], 8);
+    out->particle_iterations = (int64_t)cnt[CNT_PIT];
+    out->ls_moves = (int64_t)cnt[CNT_MOVES];
+    out->ls_rounds = (int64_t)cnt[CNT_ROUNDS];
+    out->delta_full = (int64_t)cnt[CNT_DELTA_FULL];
+    out->delta_incr = (int64_t)cnt[CNT_DELTA_INCR];
+    out->sx_ties = (int64_t)cnt[CNT_TIES];
+    out->errors = (int64_t)cnt[CNT_ERR];
+    return QAP_OK;
+}
+
+void pso_destroy(pso_state_t s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->g16) cudaGraphExecDestroy(s->g16);
+    cudaFree(s->dbase);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int pso_export_state(pso_state_t s, pso_host_state_t* o) {
+    if (!s || !o) return QAP_ERR_INVALID_ARG;
+    const StateView& sv = s->sv;
+    const int n = sv.n, P = sv.P, m = sv.m, ps = sv.ps;
+    const bool bf = s->prm.v_storage == PSO_V_BF16;
+    const size_t esz = bf ? 2 : 4;
+    std::vector<char> V((size_t)P * sv.vstride * esz);
+    std::vector<uint8_t> X((size_t)P * ps), Xs((size_t)P * ps), PL((size_t)P * ps), PG((size_t)m * ps), B(ps);
+    std::vector<int64_t> cL(P), c(P), cG(m);
+    std::vector<int32_t> mv(P);
+    int64_t bc = 0;
+    int32_t bi = 0, t = 0;
+    cudaStream_t st = s->stream;
+    cudaError_t e = cudaMemcpyAsync(V.data(), sv.V, V.size(), cudaMemcpyDeviceToHost, st);
+    auto cp = [&](void* dst, const void* src, size_t b) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, st);
+    };
+    cp(X.data(), sv.X, X.size());
+    cp(Xs.data(), sv.Xsx, Xs.size());
+    cp(PL.data(), sv.PL, PL.size());
+    cp(PG.data(), sv.PG, PG.size());
+    cp(B.data(), sv.best, B.size());
+    cp(cL.data(), sv.costL, P * 8);
+    cp(c.data(), sv.cost, P * 8);
+    cp(cG.data(), sv.costG, m * 8);
+    cp(mv.data(), sv.moves, P * 4);
+    cp(&bc, sv.best_cost, 8);
+    cp(&bi, sv.best_iter, 4);
+    cp(&t, sv.t, 4);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return status_of(e);
+    for (int p = 0; p < P; ++p) {
+        for (int k = 0; k < n * n; ++k) {
+            const size_t idx = (size_t)p * sv.vstride + k;
+            float f;
+            if (bf) {
+                uint16_t h;
+                std::memcpy(&h, V.data() + idx * 2, 2);
+                f = host_from_bf16(h);
+            } else {
+                std::memcpy(&f, V.data() + idx * 4, 4);
+            }
+            if (o->V) o->V[(size_t)p * n * n + k] = f;
+        }
+        for (int j = 0; j < n; ++j) {
+            if (o->X) o->X[(size_t)p * n + j] = X[(size_t)p * ps + j];
+            if (o->X_sx) o->X_sx[(size_t)p * n + j] = Xs[(size_t)p * ps + j];
+            if (o->PL) o->PL[(size_t)p * n + j] = PL[(size_t)p * ps + j];
+        }
+        if (o->costL) o->costL[p] = cL[p];
+        if (o->cost) o->cost[p] = c[p];
+        if (o->moves) o->moves[p] = mv[p];
+    }
+    for (int k = 0; k < m; ++k) {
+        for (int j = 0; j < n; ++j)
+            if (o->PG) o->PG[(size_t)k * n + j] = PG[(size_t)k * ps + j];
+        if (o->costG) o->costG[k] = cG[k];
+    }
+    if (o->best)
+        for (int j = 0; j < n; ++j) o->best[j] = B[j];
+    o->best_cost = bc;
+    o->best_iter = bi;
+    o->t = t;
+    return QAP_OK;
+}
+
+int pso_import_state(pso_state_t s, const pso_host_state_t* in) {
+    if (!s || !in || !in->V || !in->X || !in->PL || !in->costL || !in->cost || !in->PG ||
+        !in->costG || !in->best)
+        return QAP_ERR_INVALID_ARG;
+    const StateView& sv = s->sv;
+    const int n = sv.n, P = sv.P, m = sv.m, ps = sv.ps;
+    const bool bf = s->prm.v_storage == PSO_V_BF16;
+    const size_t esz = bf ? 2 : 4;
+    auto perm_ok = [n](const int32_t* p) {
+        std::vector<char> seen(n, 0);
+        for (int j = 0; j < n; ++j) {
+            if (p[j] < 0 || p[j] >= n || seen[p[j]]) return false;
+            seen[p[j]] = 1;
+        }
+        return true;
+    };
+    for (int p = 0; p < P; ++p)
+        if (!perm_ok(in->X + (size_t)p * n) || !perm_ok(in->PL + (size_t)p * n)) return QAP_ERR_INVALID_ARG;
+    for (int k = 0; k < m; ++k)
+        if (!perm_ok(in->PG + (size_t)k * n)) return QAP_ERR_INVALID_ARG;
+    if (!perm_ok(in->best) || in->t < 0) return QAP_ERR_INVALID_ARG;
+    std::vector<char> V((size_t)P * sv.vstride * esz, 0);
+    std::vector<uint8_t> X((size_t)P * ps, 0), PL((size_t)P * ps, 0), PG((size_t)m * ps, 0), B(ps, 0);
+    for (int p = 0; p < P; ++p) {
+        for (int k = 0; k < n * n; ++k) {
+            const float f = in->V[(size_t)p * n * n + k];
+            const size_t idx = (size_t)p * sv.vstride + k;
+            if (bf) {
+                const uint16_t h = host_bf16(f);
+                std::memcpy(V.data() + idx * 2, &h, 2);
+            } else {
+                std::memcpy(V.data() + idx * 4, &f, 4);
+            }
+        }
+        for (int j = 0; j < n; ++j) {
+            X[(size_t)p * ps + j] = (uint8_t)in->X[(size_t)p * n + j];
+            PL[(size_t)p * ps + j] = (uint8_t)in->PL[(size_t)p * n + j];
+        }
+    }
+    for (int k = 0; k < m; ++k)
+        for (int j = 0; j < n; ++j) PG[(size_t)k * ps + j] = (uint8_t)in->PG[(size_t)k * n + j];
+    for (int j = 0; j < n; ++j) B[j] = (uint8_t)in->best[j];
+    cudaStream_t st = s->stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    auto cp = [&](void* dst, const void* src, size_t b) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st);
+    };
+    cp(sv.V, V.data(), V.size());
+    cp(sv.X, X.data(), X.size());
+    cp(sv.PL, PL.data(), PL.size());
+    cp(sv.PG, PG.data(), PG.size());
+    cp(sv.best, B.data(), B.size());
+    cp(sv.costL, in->costL, P * 8);
+    cp(sv.cost, in->cost, P * 8);
+    cp(sv.costG, in->costG, m * 8);
+    cp(sv.best_cost, &in->best_cost, 8);
+    cp(sv.best_iter, &in->best_iter, 4);
+    cp(sv.t, &in->t, 4);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return status_of(e);
+}
+
+static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count, int32_t max_moves,
+                       int32_t* perms_out, int64_t* costs, int32_t* moves, int32_t* rounds) {
+    const int n = inst->n;
+    for (int c = 0; c < count; ++c) {
+        std::vector<char> seen(n, 0);
+        for (int j = 0; j < n; ++j) {
+            const int32_t v = perms[(size_t)c * n + j];
+            if (v < 0 || v >= n || seen[v]) return QAP_ERR_INVALID_ARG;
+            seen[v] = 1;
+        }
+    }
+    const int ps = (int)align_up(n, 16);
+    std::vector<uint8_t> hp((size_t)count * ps, 0);
+    for (int c = 0; c < count; ++c)
+        for (int j = 0; j < n; ++j) hp[(size_t)c * ps + j] = (uint8_t)perms[(size_t)c * n + j];
+    uint8_t *din = nullptr, *dout = nullptr;
+    int64_t* dc = nullptr;
+    int32_t *dm = nullptr, *dr = nullptr;
+    cudaError_t e = cudaMalloc(&din, hp.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dout, hp.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dc, (size_t)count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dm, (size_t)count * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dr, (size_t)count * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(din, hp.data(), hp.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        LsArgs a{};
+        a.n = n;
+        a.count = count;
+        a.ps_in = a.ps_out = ps;
+        a.F = inst->dF;
+        a.D = inst->dD;
+        a.in = din;
+        a.out = dout;
+        a.cost = dc;
+        a.moves = dm;
+        a.rounds = dr;
+        a.max_moves = max_moves;
+        e = launch_ls(a, 0);
+    }
+    std::vector<int64_t> hc(count);
+    std::vector<int32_t> hm(count), hr(count);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(hp.data(), dout, hp.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hc.data(), dc, (size_t)count * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hm.data(), dm, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hr.data(), dr, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    cudaFree(din);
+    cudaFree(dout);
+    cudaFree(dc);
+    cudaFree(dm);
+    cudaFree(dr);
+    if (e != cudaSuccess) return status_of(e);
+    for (int c = 0; c < count; ++c) {
+        if (perms_out)
+            for (int j = 0; j < n; ++j) perms_out[(size_t)c * n + j] = hp[(size_t)c * ps + j];
+        if (costs) costs[c] = hc[c];
+        if (moves) moves[c] = hm[c];
+        if (rounds) rounds[c] = hr[c];
+    }
+    return QAP_OK;
+}
+
+int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int64_t* out) {
+    if (!inst || !perms || !out || count < 0) return QAP_ERR_INVALID_ARG;
+    if (count == 0) return QAP_OK;
+    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
+    if (inst->n > ls_max_n()) return QAP_ERR_UNSUPPORTED;
+    return run_ls_hook(inst, perms, count, -1, nullptr, out, nullptr, nullptr);
+}
+
+int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
+                     int64_t* costs, int32_t* moves, int32_t* rounds) {
+    if (!inst || !perms || count < 0 || max_moves < 0) return QAP_ERR_INVALID_ARG;
+    if (count == 0) return QAP_OK;
+    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
+    if (!inst->sym_zd) return QAP_ERR_UNSUPPORTED;
+    if (inst->n > ls_max_n()) return QAP_ERR_UNSUPPORTED;
+    return run_ls_hook(inst, perms, count, max_moves, perms, costs, moves, rounds);
+}
+
+}  // extern "C"

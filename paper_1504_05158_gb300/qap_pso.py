@@ -1,0 +1,262 @@
+"""Thin ctypes binding of ``libqap_pso.so`` (C-ABI in include/qap_pso.h).
+
+Argument marshalling only: every step of the PSO iteration runs in the CUDA
+library. Loading fails loudly if the library has not been built; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqap_pso.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
+SV_RAW, SV_NORM = 0, 1
+SX_ALG1, SX_TOPD = 0, 1
+TIE_RANDOM, TIE_FIRST = 0, 1
+MIG_NONE, MIG_RANK, MIG_RING = 0, 1, 2
+V_FP32, V_BF16 = 0, 1
+
+# every exported symbol of include/qap_pso.h
+EXPORTS = [
+    "qap_status_string", "qap_create_instance", "qap_destroy_instance", "qap_instance_info",
+    "pso_params_default", "pso_init", "pso_step", "pso_step_timed", "pso_best", "pso_stats", "pso_destroy",
+    "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
+]
+
+
+class QapError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("swarms", C.c_int32), ("swarm_size", C.c_int32),
+        ("c1", C.c_float), ("c2", C.c_float), ("c3", C.c_float),
+        ("sv_kind", C.c_int32), ("v_max", C.c_float),
+        ("sx_rule", C.c_int32), ("depth", C.c_int32), ("tie_rule", C.c_int32),
+        ("pos_uses_new_v", C.c_int32), ("ls_max_moves", C.c_int32), ("ls_at_init", C.c_int32),
+        ("mig_kind", C.c_int32), ("mig_depth", C.c_int32), ("mig_period", C.c_int32),
+        ("ring_if_better", C.c_int32), ("v_storage", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("size", C.c_uint32), ("iteration", C.c_int32), ("best_cost", C.c_int64),
+        ("min", C.c_int64), ("p5", C.c_int64), ("p25", C.c_int64), ("p50", C.c_int64),
+        ("p75", C.c_int64), ("max", C.c_int64), ("mean", C.c_double),
+        ("particle_iterations", C.c_int64), ("ls_moves", C.c_int64), ("ls_rounds", C.c_int64),
+        ("delta_full", C.c_int64), ("delta_incr", C.c_int64), ("sx_ties", C.c_int64),
+        ("errors", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "size"}
+
+
+class InstanceInfo(C.Structure):
+    _fields_ = [("n", C.c_int32), ("symmetric_zero_diag", C.c_int32), ("max_f", C.c_int32),
+                ("max_d", C.c_int32), ("exact_int32", C.c_int32)]
+
+
+class HostState(C.Structure):
+    _fields_ = [
+        ("V", C.POINTER(C.c_float)), ("X", C.POINTER(C.c_int32)), ("X_sx", C.POINTER(C.c_int32)),
+        ("PL", C.POINTER(C.c_int32)), ("costL", C.POINTER(C.c_int64)), ("cost", C.POINTER(C.c_int64)),
+        ("moves", C.POINTER(C.c_int32)), ("PG", C.POINTER(C.c_int32)), ("costG", C.POINTER(C.c_int64)),
+        ("best", C.POINTER(C.c_int32)), ("best_cost", C.c_int64), ("best_iter", C.c_int32),
+        ("t", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.qap_status_string.argtypes = [C.c_int]
+        L.qap_status_string.restype = C.c_char_p
+        L.qap_create_instance.argtypes = [C.c_int32, vp, vp, C.POINTER(vp)]
+        L.qap_destroy_instance.argtypes = [vp]
+        L.qap_destroy_instance.restype = None
+        L.qap_instance_info.argtypes = [vp, C.POINTER(InstanceInfo)]
+        L.pso_params_default.argtypes = [C.POINTER(Params)]
+        L.pso_params_default.restype = None
+        L.pso_init.argtypes = [vp, C.POINTER(Params), C.c_uint64, vp, C.POINTER(vp)]
+        L.pso_step.argtypes = [vp, C.c_int32]
+        L.pso_step_timed.argtypes = [vp, C.c_int32, vp, C.c_size_t, C.POINTER(C.c_float)]
+        L.pso_best.argtypes = [vp, C.POINTER(C.c_int64), vp, C.POINTER(C.c_int32)]
+        L.pso_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.pso_destroy.argtypes = [vp]
+        L.pso_destroy.restype = None
+        L.pso_export_state.argtypes = [vp, C.POINTER(HostState)]
+        L.pso_import_state.argtypes = [vp, C.POINTER(HostState)]
+        L.qap_eval_costs.argtypes = [vp, vp, C.c_int32, vp]
+        L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def status_string(st):
+    try:
+        return lib().qap_status_string(st).decode()
+    except Exception:
+        return str(st)
+
+
+def _check(st, what):
+    if st != OK:
+        raise QapError(st, what)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().pso_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Instance:
+    """A QAP instance resident on the device (F, D copied at construction)."""
+
+    def __init__(self, F, D):
+        F = np.ascontiguousarray(F, np.int32)
+        D = np.ascontiguousarray(D, np.int32)
+        if F.shape != D.shape or F.ndim != 2 or F.shape[0] != F.shape[1]:
+            raise ValueError("F and D must be square and of equal size")
+        self.n = F.shape[0]
+        h = C.c_void_p()
+        _check(lib().qap_create_instance(self.n, _ptr(F), _ptr(D), C.byref(h)), "qap_create_instance")
+        self.h = h
+
+    def info(self):
+        i = InstanceInfo()
+        _check(lib().qap_instance_info(self.h, C.byref(i)), "qap_instance_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def eval_costs(self, perms):
+        perms = np.ascontiguousarray(perms, np.int32).reshape(-1, self.n)
+        out = np.zeros(len(perms), np.int64)
+        _check(lib().qap_eval_costs(self.h, _ptr(perms), len(perms), _ptr(out)), "qap_eval_costs")
+        return out
+
+    def local_search(self, perms, max_moves=0):
+        perms = np.ascontiguousarray(perms, np.int32).reshape(-1, self.n).copy()
+        k = len(perms)
+        costs = np.zeros(k, np.int64)
+        moves = np.zeros(k, np.int32)
+        rounds = np.zeros(k, np.int32)
+        _check(lib().qap_local_search(self.h, _ptr(perms), k, max_moves, _ptr(costs), _ptr(moves),
+                                      _ptr(rounds)), "qap_local_search")
+        return perms, costs, moves, rounds
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qap_destroy_instance(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Swarm:
+    """Population state of one PSO run on the device."""
+
+    def __init__(self, inst: Instance, params: Params, seed: int, stream=None):
+        self.inst = inst  # keeps the instance alive
+        self.params = params
+        self.n = inst.n
+        self.P = params.swarms * params.swarm_size
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        _check(lib().pso_init(inst.h, C.byref(params), seed, st, C.byref(h)), "pso_init")
+        self.h = h
+
+    def step(self, iterations=1):
+        _check(lib().pso_step(self.h, iterations), "pso_step")
+
+    def step_timed(self, iterations=1, flush_ptr=None, flush_bytes=0):
+        """Runs iterations with per-kernel device times; returns milliseconds of
+        [velocity + S_x, goal function + local search, bests + migration, span]."""
+        ms = (C.c_float * 4)()
+        fp = C.c_void_p(flush_ptr) if flush_ptr else None
+        _check(lib().pso_step_timed(self.h, iterations, fp, flush_bytes, ms), "pso_step_timed")
+        return [ms[0], ms[1], ms[2], ms[3]]
+
+    def best(self):
+        c = C.c_int64()
+        it = C.c_int32()
+        perm = np.zeros(self.n, np.int32)
+        _check(lib().pso_best(self.h, C.byref(c), _ptr(perm), C.byref(it)), "pso_best")
+        return c.value, perm, it.value
+
+    def stats(self):
+        s = Stats()
+        s.size = C.sizeof(Stats)
+        _check(lib().pso_stats(self.h, C.byref(s)), "pso_stats")
+        return s.as_dict()
+
+    def export_state(self):
+        n, P, m = self.n, self.P, self.params.swarms
+        a = dict(V=np.zeros((P, n, n), np.float32), X=np.zeros((P, n), np.int32),
+                 X_sx=np.zeros((P, n), np.int32), PL=np.zeros((P, n), np.int32),
+                 costL=np.zeros(P, np.int64), cost=np.zeros(P, np.int64),
+                 moves=np.zeros(P, np.int32), PG=np.zeros((m, n), np.int32),
+                 costG=np.zeros(m, np.int64), best=np.zeros(n, np.int32))
+        hs = HostState()
+        for k, v in a.items():
+            ty = {np.float32: C.c_float, np.int32: C.c_int32, np.int64: C.c_int64}[v.dtype.type]
+            setattr(hs, k, v.ctypes.data_as(C.POINTER(ty)))
+        _check(lib().pso_export_state(self.h, C.byref(hs)), "pso_export_state")
+        a["best_cost"], a["best_iter"], a["t"] = hs.best_cost, hs.best_iter, hs.t
+        return a
+
+    def import_state(self, a):
+        hs = HostState()
+        keep = {}
+        for k, dt, ty in (("V", np.float32, C.c_float), ("X", np.int32, C.c_int32),
+                          ("PL", np.int32, C.c_int32), ("costL", np.int64, C.c_int64),
+                          ("cost", np.int64, C.c_int64), ("PG", np.int32, C.c_int32),
+                          ("costG", np.int64, C.c_int64), ("best", np.int32, C.c_int32)):
+            v = np.ascontiguousarray(a[k], dt)
+            keep[k] = v
+            setattr(hs, k, v.ctypes.data_as(C.POINTER(ty)))
+        hs.best_cost, hs.best_iter, hs.t = int(a["best_cost"]), int(a["best_iter"]), int(a["t"])
+        _check(lib().pso_import_state(self.h, C.byref(hs)), "pso_import_state")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pso_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

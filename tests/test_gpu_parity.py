@@ -1,0 +1,235 @@
+"""CUDA path against the oracle, element by element, on identical seeded inputs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1504_05158_gb300 import workloads as W
+from tests.replay import check_velocity, compare_step, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1504_05158_gb300 import qap_pso
+    qap_pso.lib()
+    return qap_pso
+
+
+INSTANCES = {
+    "n2": lambda: W.dense_uniform(2, 1),
+    "n3": lambda: W.dense_uniform(3, 2),
+    "tiny9": W.tiny9,
+    "dense30": W.dense30,
+    "n33": lambda: W.dense_uniform(33, 5),
+    "grid64": W.grid64,
+    "n65grid": lambda: W.grid_sparse(65, 6),
+    "n100": lambda: W.dense_uniform(100, 7),
+    "n128grid": lambda: W.grid_sparse(128, 8),
+    "n150": lambda: W.dense_uniform(150, 9),
+}
+
+
+# ------------------------------------------------------------ goal function
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_eval_costs_bit_exact(Q, name):
+    inst = INSTANCES[name]()
+    gi = Q.Instance(inst.F, inst.D)
+    perms = W.random_perms(77, inst.n, 3)
+    got = gi.eval_costs(perms)
+    want = np.array([O.cost(inst.F, inst.D, p) for p in perms])
+    assert np.array_equal(got, want)
+
+
+def test_eval_costs_general_instance(Q):
+    inst = W.random_asymmetric(21, 4, hi=200)
+    gi = Q.Instance(inst.F, inst.D)
+    assert gi.info()["symmetric_zero_diag"] == 0
+    perms = W.random_perms(40, 21, 4)
+    assert np.array_equal(gi.eval_costs(perms), [O.cost(inst.F, inst.D, p) for p in perms])
+
+
+# ------------------------------------------------------------ local search
+
+@pytest.mark.parametrize("name", list(INSTANCES))
+@pytest.mark.parametrize("cap", [0, 3])
+def test_local_search_bit_exact(Q, name, cap):
+    inst = INSTANCES[name]()
+    gi = Q.Instance(inst.F, inst.D)
+    count = 40 if inst.n <= 64 else 9
+    perms = W.random_perms(count, inst.n, 11)
+    gp, gc, gm, gr = gi.local_search(perms, cap)
+    for i, p in enumerate(perms):
+        op, oc, om, orr, _ = O.local_search(inst.F, inst.D, p, cap)
+        assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om and gr[i] == orr, i
+
+
+def test_local_search_rejects_bad_input(Q):
+    inst = W.dense_uniform(8, 1)
+    gi = Q.Instance(inst.F, inst.D)
+    with pytest.raises(Q.QapError):
+        gi.local_search(np.zeros((1, 8), np.int32))  # not a permutation
+    asym = W.random_asymmetric(8, 2)
+    ga = Q.Instance(asym.F, asym.D)
+    with pytest.raises(Q.QapError) as e:
+        ga.local_search(W.random_perms(1, 8, 1))
+    assert e.value.status == Q.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------ init
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_init_bit_exact(Q, storage):
+    inst = W.dense30()
+    prm = Q.default_params(swarms=3, swarm_size=37, v_storage=storage, v_max=0.75)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=123)
+    st = sw.export_state()
+    q = oracle_params(prm)
+    o = O.init(q, inst.F, inst.D, 123)
+    assert np.array_equal(st["X"], o.X) and np.array_equal(st["cost"], o.cost)
+    assert np.array_equal(st["V"].astype(np.float64), o.V)
+    assert np.array_equal(st["PL"], o.PL) and np.array_equal(st["costL"], o.costL)
+    assert np.array_equal(st["PG"], o.PG) and np.array_equal(st["costG"], o.costG)
+    assert st["best_cost"] == o.best_cost[0] and np.array_equal(st["best"], o.best_p)
+    assert st["t"] == 0 and st["best_iter"] == 0
+
+
+# ------------------------------------------------------------ whole iterations
+
+VARIANTS = {
+    "default": dict(),
+    "raw": dict(sv_kind=0, v_max=0.5),
+    "topd": dict(sx_rule=1, depth=3),
+    "globalmax": dict(depth=0),
+    "tiefirst": dict(tie_rule=1, sv_kind=0, v_max=0.25),
+    "newv": dict(pos_uses_new_v=1),
+    "bf16": dict(v_storage=1),
+    "nols": dict(ls_max_moves=-1),
+    "lscap": dict(ls_max_moves=2, ls_at_init=1),
+    "rank": dict(mig_kind=1, mig_depth=1, mig_period=1),
+    "ring": dict(mig_kind=2, mig_period=2),
+    "ringbetter": dict(mig_kind=2, mig_period=1, ring_if_better=1),
+}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("name,m,ss", [("tiny9", 2, 16), ("dense30", 3, 21), ("grid64", 4, 13)])
+def test_iterations_replay(Q, variant, name, m, ss):
+    inst = INSTANCES[name]()
+    kw = dict(swarms=m, swarm_size=ss)
+    kw.update(VARIANTS[variant])
+    prm = Q.default_params(**kw)
+    seed = 1000 + m
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=seed)
+    q = oracle_params(prm)
+    before = sw.export_state()
+    for _ in range(3):
+        sw.step(1)
+        after = sw.export_state()
+        compare_step(q, inst.F, inst.D, seed, before, after, prm)
+        before = after
+
+
+@pytest.mark.parametrize("name", ["n2", "n3", "n65grid", "n100", "n150"])
+def test_iterations_replay_edge_sizes(Q, name):
+    inst = INSTANCES[name]()
+    prm = Q.default_params(swarms=2, swarm_size=5, depth=min(2, inst.n - 1), mig_kind=1,
+                           mig_depth=0)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=5)
+    q = oracle_params(prm)
+    before = sw.export_state()
+    for _ in range(2):
+        sw.step(1)
+        after = sw.export_state()
+        compare_step(q, inst.F, inst.D, 5, before, after, prm)
+        before = after
+
+
+def test_ties_from_imported_state(Q):
+    # velocities in {-1, 0, 1}: most S_x steps see several equal maxima
+    inst = W.dense_uniform(20, 3)
+    for rule in (0, 1):
+        prm = Q.default_params(swarms=2, swarm_size=9, sv_kind=0, depth=3, sx_rule=rule)
+        sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=9)
+        st = sw.export_state()
+        rng = np.random.default_rng(rule)
+        st["V"] = rng.integers(-1, 2, st["V"].shape).astype(np.float32)
+        sw.import_state(st)
+        before = sw.export_state()
+        sw.step(1)
+        after = sw.export_state()
+        compare_step(oracle_params(prm), inst.F, inst.D, 9, before, after, prm)
+        assert sw.stats()["sx_ties"] > 0
+
+
+def test_full_size_grid64_sampled(Q):
+    # the n = 64, 16 x 640 workload, with ring migration every 20 iterations
+    inst = W.grid64()
+    for storage in (0, 1):
+        prm = Q.default_params(swarms=16, swarm_size=640, mig_kind=2, mig_period=20,
+                               v_storage=storage)
+        sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=64)
+        q = oracle_params(prm)
+        sw.step(18)
+        before = sw.export_state()
+        rng = np.random.default_rng(storage)
+        for _ in range(3):  # iterations 19, 20 (ring), 21
+            sw.step(1)
+            after = sw.export_state()
+            sample = np.concatenate([[0, 639, 640, 10239], rng.choice(10240, 28, replace=False)])
+            compare_step(q, inst.F, inst.D, 64, before, after, prm, sample=sample)
+            before = after
+
+
+def test_full_size_dense30_sampled(Q):
+    inst = W.dense30()
+    prm = Q.default_params(swarms=10, swarm_size=1000)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=30)
+    before = sw.export_state()
+    sw.step(1)
+    after = sw.export_state()
+    compare_step(oracle_params(prm), inst.F, inst.D, 30, before, after, prm,
+                 sample=np.arange(0, 10000, 313))
+
+
+# ------------------------------------------------------------ results and statistics
+
+def test_stats_and_best(Q):
+    inst = W.dense30()
+    prm = Q.default_params(swarms=5, swarm_size=200)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=77)
+    sw.step(4)
+    st = sw.export_state()
+    got = sw.stats()
+    want = O.stats(st["cost"])
+    for k in ("min", "p5", "p25", "p50", "p75", "max"):
+        assert got[k] == want[k], k
+    assert abs(got["mean"] - want["mean"]) <= 1e-9 * abs(want["mean"])
+    assert got["iteration"] == 4 and got["particle_iterations"] == 4 * 1000
+    assert got["errors"] == 0
+    assert got["ls_rounds"] == got["ls_moves"] + 4 * 1000
+    n = 30
+    assert got["delta_full"] == 4 * 1000 * n * (n - 1) // 2
+    assert got["delta_incr"] == got["ls_moves"] * n * (n - 1) // 2
+    c, perm, it = sw.best()
+    assert c == got["best_cost"] == O.cost(inst.F, inst.D, perm) and 0 <= it <= 4
+
+
+def test_tiny9_reaches_optimum(Q):
+    inst = W.tiny9()
+    opt, _ = O.brute_force(inst.F, inst.D)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), Q.default_params(swarms=1, swarm_size=32), seed=1)
+    sw.step(100)
+    c, perm, _ = sw.best()
+    assert c == opt == O.cost(inst.F, inst.D, perm)
+
+
+def test_invalid_params(Q):
+    inst = W.dense_uniform(10, 1)
+    gi = Q.Instance(inst.F, inst.D)
+    for bad in (dict(depth=10), dict(swarms=0), dict(v_max=0.0), dict(mig_kind=1, mig_depth=1,
+                                                                       swarms=2)):
+        with pytest.raises(Q.QapError) as e:
+            Q.Swarm(gi, Q.default_params(**bad), seed=1)
+        assert e.value.status == Q.ERR_INVALID_ARG

@@ -150,7 +150,10 @@ def run_ours(args, rank, world, local_rank):
     alu_peak_tops = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # int32 lanes x (mul + add) x clock
 
     results = {}
+    wanted = [v.strip() for v in args.variants.split(",") if v.strip()]
     for storage_name, storage in (("fp32", Q.V_FP32), ("bf16", Q.V_BF16)):
+        if storage_name not in wanted:
+            continue
         sw, s0, stream = measure(Q, W, torch, storage, args.steps, args.warmup, rank, flush)
         barrier()
         torch.cuda.synchronize()
@@ -187,11 +190,27 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C-ABI with host buffers: instance upload, init, K iterations
     # each followed by a read-back of the best cost and permutation
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, Q, W, torch, dist, rank, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        print(json.dumps(result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops)))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, Q, W, torch, dist, rank, world):
     inst = W.grid64()
     F = torch.from_numpy(inst.F).pin_memory()
     D = torch.from_numpy(inst.D).pin_memory()
     torch.cuda.synchronize()
-    barrier()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     gi = Q.Instance(F.numpy(), D.numpy())
     sw = Q.Swarm(gi, params(Q, Q.V_FP32), seed=640 + rank)
@@ -206,16 +225,14 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": SWARMS * SWARM_SIZE * args.steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 2 * N * N * 4 / args.steps,
-           "d2h_bytes_per_step": 8 + 4 + N,
-           "what": "qap_create_instance + pso_init + K x (pso_step(1) + pso_best), host F and D"}
+    return {"value": SWARMS * SWARM_SIZE * args.steps * world / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * N * N * 4 / args.steps,
+            "d2h_bytes_per_step": 8 + 4 + N,
+            "what": "qap_create_instance + pso_init + K x (pso_step(1) + pso_best), host F and D"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
 
-    if rank == 0:
+def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
+    if True:
         r = results["fp32"]
         k1, k2 = r["kernel_ms"]["velocity_sx"], r["kernel_ms"]["cost_ls"]
         if k2 >= k1:
@@ -240,18 +257,17 @@ def run_ours(args, rank, world, local_rank):
             "alu_cost_ls": {"achieved_tops": r["k2_tops"], "peak_tops": alu_peak_tops,
                             "frac": r["k2_tops"] / alu_peak_tops},
             "roofline": roof,
-            "bf16": {k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
-                                                      "kernel_ms", "k1_gbs", "best_cost")},
-            "quality": {"fp32_best": r["best_cost"], "bf16_best": results["bf16"]["best_cost"],
-                        "bf16_vs_fp32": results["bf16"]["best_cost"] / r["best_cost"] - 1.0,
-                        "iterations": r["iterations"]},
+            "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
+                                                       "kernel_ms", "k1_gbs", "best_cost")}
+                     if "bf16" in results else None),
+            "quality": ({"fp32_best": r["best_cost"], "bf16_best": results["bf16"]["best_cost"],
+                         "bf16_vs_fp32": results["bf16"]["best_cost"] / r["best_cost"] - 1.0,
+                         "iterations": r["iterations"]} if "bf16" in results else None),
             "moves_per_particle_iteration": r["moves_per_pit"],
             "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line))
-    if dist:
-        dist.destroy_process_group()
+        return line
 
 
 # ----------------------------------------------------------------------- oracle
@@ -310,6 +326,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variants", default="fp32,bf16",
+                    help="velocity storage formats to time (fp32 is the headline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -24,6 +24,7 @@ namespace qap {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr size_t kBarBytes = 64;  // one mbarrier per warp, ahead of the tiles
 constexpr size_t kSmemLimit = 227 * 1024;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -34,7 +35,7 @@ __host__ __device__ inline size_t tile_bytes(int n) {
 }
 template <typename VT>
 __host__ __device__ inline size_t warp_bytes(int n) {
-    return tile_bytes<VT>(n) + align16((size_t)n);
+    return tile_bytes<VT>(n) + 32;  // + deleted-row bits (8 words)
 }
 
 // --------------------------------------------------------------------- init
@@ -85,182 +86,296 @@ __global__ void k_init(StateView s) {
 }
 
 // --------------------------------------------------------- velocity and S_x
-template <int NW, typename VT>
-__device__ __forceinline__ float yval(const VT* tile, int n, int i, int col, int pic) {
-    return VStore<VT>::to_f(tile[i * n + col]) + (pic == i ? 1.0f : 0.0f);
-}
+// Per-column cache of the largest plain velocity value V[i][c] over the remaining
+// rows i other than the column's X(t) row pz: value, multiplicity, first row. The
+// X(t) cell itself, Y[pz][c] = V[pz][c] + 1, is kept apart, so ignoring it (the
+// first `depth` steps) or losing it (row pz assigned) never forces a rescan. A
+// cache whose copies of the maximum have all been deleted keeps its value as an
+// upper bound (count 0) and is rescanned only when needed; +inf means never
+// scanned, -inf means no rows left. Deleted rows are bits of `dead` (shared memory,
+// one word per 32 rows). The scan reads 32 rows at a time with independent loads.
+struct ColMax {
+    float v;
+    int cnt, first;
+};
 
-// maximum key and its multiplicity over the remaining rows of one column
 template <typename VT>
-__device__ __forceinline__ void col_scan(const VT* tile, const uint8_t* rowdead, int n, int col,
-                                         int pic, int exrow, uint32_t& key, int& cnt) {
-    uint32_t mx = 0;
-    int c = 0;
-    for (int i = 0; i < n; ++i) {
-        if (rowdead[i] || i == exrow) continue;
-        const uint32_t k = fkey(VStore<VT>::to_f(tile[i * n + col]) + (pic == i ? 1.0f : 0.0f));
-        if (k > mx) {
-            mx = k;
-            c = 1;
-        } else if (k == mx) {
-            ++c;
+__device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz) {
+    const float kNegInf = __int_as_float(0xff800000);
+    ColMax r{kNegInf, 0, -1};
+    for (int base = 0; base < n; base += 32) {
+        uint32_t ok = ~dead[base >> 5];
+        if ((pz >> 5) == (base >> 5)) ok &= ~(1u << (pz & 31));
+        const int lim = n - base;
+        if (lim < 32) ok &= (1u << lim) - 1u;
+        float v[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b)
+            v[b] = ((ok >> b) & 1u) ? VStore<VT>::to_f(tile[(base + b) * n + c]) : kNegInf;
+        float mx = v[0];
+#pragma unroll
+        for (int b = 1; b < 32; ++b) mx = fmaxf(mx, v[b]);
+        uint32_t eq = 0u;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) eq |= (((ok >> b) & 1u) && v[b] == mx) ? (1u << b) : 0u;
+        if (eq) {
+            if (r.cnt == 0 || mx > r.v) {
+                r.v = mx;
+                r.cnt = __popc(eq);
+                r.first = base + __ffs(eq) - 1;
+            } else if (mx == r.v) {
+                r.cnt += __popc(eq);
+            }
         }
     }
-    key = mx;
-    cnt = c;
+    return r;
 }
 
+// first remaining row after r (other than pz) holding value vm in column c, or -1
+template <typename VT>
+__device__ __noinline__ int vnext(const VT* tile, const uint32_t* dead, int n, int c, int pz, float vm,
+                                  int r) {
+    for (int i = r + 1; i < n; ++i)
+        if (!((dead[i >> 5] >> (i & 31)) & 1u) && i != pz && VStore<VT>::to_f(tile[i * n + c]) == vm)
+            return i;
+    return -1;
+}
+
+// the kk-th remaining row (ascending) of column c whose Y value equals e, where the
+// X(t) row pz counts with value zv when the X(t) cell takes part (zin)
+template <typename VT>
+__device__ __noinline__ int kth_row(const VT* tile, const uint32_t* dead, int n, int c, int pz, bool zin,
+                                    float zv, float e, int kk) {
+    int seen = 0;
+    for (int i = 0; i < n; ++i) {
+        if ((dead[i >> 5] >> (i & 31)) & 1u) continue;
+        const bool hit = (i == pz) ? (zin && zv == e) : (VStore<VT>::to_f(tile[i * n + c]) == e);
+        if (hit) {
+            if (seen == kk) return i;
+            ++seen;
+        }
+    }
+    return -1;
+}
+
+// SecondTarget (Algorithm 1) on Y = X(t) + tile for one particle; returns the
+// number of steps whose set M had more than one element and leaves the location
+// chosen for each owned column (facility) in newp.
+//
+// After the first `depth` steps, every X(t) cell that exceeds all remaining plain
+// values (bound P0) is taken by the greedy in descending order over consecutive
+// steps, each in its own row and column, so such cells are assigned together in
+// one round; equal values among them only reorder those steps (each group of g
+// equal values is g - 1 steps with a choice). Other steps run one at a time.
 template <int NW, typename VT>
-__global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = s.n;
-    VT* tile = reinterpret_cast<VT*>(smem + warp * warp_bytes<VT>(n));
-    uint8_t* rowdead = smem + warp * warp_bytes<VT>(n) + tile_bytes<VT>(n);
-    const uint32_t t = (uint32_t)*s.t;
-    const bool norm = s.sv_kind == 1;
-
-    for (int p = blockIdx.x * kWarps + warp; p < s.P; p += gridDim.x * kWarps) {
-        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
-        int pic[NW], plc[NW], pgc[NW];
+__device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, int n,
+                                             int lane, const int (&pic)[NW], uint32_t pis,
+                                             uint32_t swarm, uint32_t t, int (&newp)[NW]) {
+    const int depth = s.depth;
+    if (lane < NW) dead[lane] = 0u;
+    __syncwarp();
+    float zv[NW], vm[NW];
+    int vc[NW], va[NW];
+    bool alive[NW], zal[NW], ex[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int j = lane + 32 * w;
-            pic[w] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
-            plc[w] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[w] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
-        }
-        // stage V(t) in shared memory (16-byte chunks; the tile is padded to 16 bytes)
-        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
-        {
-            const uint4* src = reinterpret_cast<const uint4*>(Vg);
-            uint4* dst = reinterpret_cast<uint4*>(tile);
-            const int chunks = (int)(tile_bytes<VT>(n) / 16);
-            for (int c = lane; c < chunks; c += 32) dst[c] = src[c];
-        }
-        for (int i = lane; i < n; i += 32) rowdead[i] = 0;
-        __syncwarp();
-
-        // ---- Eq. 4 ----
-        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
-        float inv[NW];
+    for (int w = 0; w < NW; ++w) {
+        const int c = lane + 32 * w;
+        alive[w] = c < n;
+        zal[w] = alive[w];
+        ex[w] = false;
+        zv[w] = alive[w] ? VStore<VT>::to_f(tile[pic[w] * n + c]) + 1.0f : 0.0f;
+        vm[w] = __int_as_float(0x7f800000);
+        vc[w] = 0;
+        va[w] = -1;
+        newp[w] = 0;
+    }
+    if (depth > 0) {
+        if (s.sx_rule == 0) {
+            // Algorithm 1 as printed: every element equal to 1 in Z = X(t) is ignored
 #pragma unroll
-        for (int w = 0; w < NW; ++w) inv[w] = 1.0f;
-        if (norm) {
-            float sum[NW];
+            for (int w = 0; w < NW; ++w) ex[w] = alive[w];
+        } else {
+            // the `depth` largest of them (lower column first on ties)
+            for (int d = 0; d < depth; ++d) {
+                uint32_t lm = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) sum[w] = 0.0f;
-            for (int i = 0; i < n; ++i) {
+                for (int w = 0; w < NW; ++w)
+                    if (alive[w] && !ex[w]) lm = max(lm, fkey(zv[w]));
+                const uint32_t gm = __reduce_max_sync(FULL, lm);
+                bool done = false;
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
-                    const int j = lane + 32 * w;
-                    if (j < n) {
-                        const float v = VStore<VT>::to_f(tile[i * n + j]);
-                        const float dl = (float)((plc[w] == i) - (pic[w] == i));
-                        const float dg = (float)((pgc[w] == i) - (pic[w] == i));
-                        float x = fmaf(s.c1, v, a * dl + b * dg);
-                        x = fminf(fmaxf(x, -s.v_max), s.v_max);
-                        sum[w] += fabsf(x);
+                    if (done) continue;
+                    const unsigned bal = __ballot_sync(FULL, alive[w] && !ex[w] && fkey(zv[w]) == gm);
+                    if (bal) {
+                        if (lane == __ffs(bal) - 1) ex[w] = true;
+                        done = true;
                     }
                 }
             }
-#pragma unroll
-            for (int w = 0; w < NW; ++w) inv[w] = sum[w] > 0.0f ? 1.0f / sum[w] : 1.0f;
         }
-        const bool newv = s.pos_uses_new_v != 0;
-        for (int i = 0; i < n; ++i) {
+    }
+    int ties = 0;
+    for (int step = 0; step < n;) {
+        const bool use_ex = step < depth;
+        bool zin[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) zin[w] = alive[w] && zal[w] && !(use_ex && ex[w]);
+
+        if (!use_ex) {
+            // ---- a round of X(t) cells above every remaining plain value ----
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (alive[w] && !zin[w] && vc[w] == 0) {
+                    const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w]);
+                    vm[w] = cm.v;
+                    vc[w] = cm.cnt;
+                    va[w] = cm.first;
+                }
+            uint32_t lp = 0u;
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (alive[w]) lp = max(lp, fkey(vm[w]));
+            const uint32_t P0 = __reduce_max_sync(FULL, lp);
+            bool inB[NW];
+            uint32_t bkey[NW];
+            unsigned any = 0u;
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                const int j = lane + 32 * w;
-                if (j < n) {
-                    const float v = VStore<VT>::to_f(tile[i * n + j]);
-                    const float dl = (float)((plc[w] == i) - (pic[w] == i));
-                    const float dg = (float)((pgc[w] == i) - (pic[w] == i));
-                    float x = fmaf(s.c1, v, a * dl + b * dg);
-                    x = fminf(fmaxf(x, -s.v_max), s.v_max);
-                    if (norm) x *= inv[w];
-                    const VT o = VStore<VT>::from_f(x);
-                    Vg[i * n + j] = o;
-                    if (newv) tile[i * n + j] = o;
-                }
+                bkey[w] = fkey(zv[w]);
+                inB[w] = zin[w] && bkey[w] > P0;
+                any |= __ballot_sync(FULL, inB[w]);
             }
-        }
-        __syncwarp();
-
-        // ---- Eq. 5: SecondTarget on Y = X(t) + V ----
-        const int depth = s.depth;
-        int exrow[NW];
+            if (any) {
+                // size of the round and the number of distinct values in it: a cell
+                // is the first of its value group when no equal cell of the round sits
+                // in a lower column (same register slot: lower lane; lower slot: any lane)
+                int mine = 0, firsts = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) exrow[w] = -1;
-        if (depth > 0) {
-            if (s.sx_rule == 0) {
+                for (int w = 0; w < NW; ++w) {
+                    const unsigned grp = __match_any_sync(FULL, inB[w] ? bkey[w] : 0xFFFFFFFFu);
+                    bool first = inB[w] && (__ffs(grp) - 1 == lane);
 #pragma unroll
-                for (int w = 0; w < NW; ++w) exrow[w] = pic[w];
-            } else {
-                uint32_t zk[NW];
+                    for (int w0 = 0; w0 < w; ++w0) {
+                        const uint32_t mk = inB[w0] ? bkey[w0] : 0xFFFFFFFFu;
+#pragma unroll 1
+                        for (int L = 0; L < 32; ++L)
+                            if (__shfl_sync(FULL, mk, L) == bkey[w]) first = false;
+                    }
+                    mine += inB[w] ? 1 : 0;
+                    firsts += first ? 1 : 0;
+                }
+                const int nb = (int)__reduce_add_sync(FULL, (unsigned)mine);
+                const int distinct = (int)__reduce_add_sync(FULL, (unsigned)firsts);
+                ties += nb - distinct;
+                // assign, delete the rows, and let the other columns lose them
+                uint32_t gone[NW];
 #pragma unroll
-                for (int w = 0; w < NW; ++w)
-                    zk[w] = pic[w] >= 0 ? fkey(yval<NW, VT>(tile, n, pic[w], lane + 32 * w, pic[w])) : 0u;
-                for (int d = 0; d < depth; ++d) {
-                    uint32_t lm = 0;
+                for (int wi = 0; wi < NW; ++wi) {
+                    uint32_t bits = 0u;
 #pragma unroll
                     for (int w = 0; w < NW; ++w)
-                        if (exrow[w] < 0 && zk[w] > lm) lm = zk[w];
-                    const uint32_t gm = __reduce_max_sync(FULL, lm);
-                    bool done = false;
+                        if (inB[w] && (pic[w] >> 5) == wi) bits |= 1u << (pic[w] & 31);
+                    gone[wi] = __reduce_or_sync(FULL, bits);
+                }
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        if (done) continue;
-                        const unsigned bal = __ballot_sync(FULL, exrow[w] < 0 && pic[w] >= 0 && zk[w] == gm);
-                        if (bal) {
-                            if (lane == __ffs(bal) - 1) exrow[w] = pic[w];
-                            done = true;
+                for (int wi = 0; wi < NW; ++wi)
+                    if (lane == wi) dead[wi] |= gone[wi];
+                __syncwarp();
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    if (inB[w]) {
+                        newp[w] = pic[w];
+                        alive[w] = false;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    if (!alive[w] || vc[w] == 0) continue;  // rows of the round are never pic[w]
+                    const int c = lane + 32 * w;
+#pragma unroll
+                    for (int wi = 0; wi < NW; ++wi) {
+                        uint32_t m = gone[wi];
+                        while (m && vc[w] > 0) {
+                            const int r = 32 * wi + __ffs(m) - 1;
+                            m &= m - 1u;
+                            if (VStore<VT>::to_f(tile[r * n + c]) == vm[w] && --vc[w] > 0 && va[w] == r)
+                                va[w] = vnext<VT>(tile, dead, n, c, pic[w], vm[w], r);
                         }
                     }
                 }
+                step += nb;
+                continue;
             }
         }
-        uint32_t ckey[NW];
-        int ccnt[NW], newp[NW];
+
+        // ---- one greedy step: the effective maximum of every owned column ----
+        uint32_t key[NW];
+        int cnt[NW], arg[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            newp[w] = 0;
-            ckey[w] = 0;
-            ccnt[w] = 0;
-            if (pic[w] >= 0)
-                col_scan<VT>(tile, rowdead, n, lane + 32 * w, pic[w], depth > 0 ? exrow[w] : -1,
-                             ckey[w], ccnt[w]);
+            key[w] = 0u;
+            cnt[w] = 0;
+            arg[w] = -1;
+            if (!alive[w]) continue;
+            if (vc[w] == 0 && !(zin[w] && zv[w] > vm[w])) {
+                const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w]);
+                vm[w] = cm.v;
+                vc[w] = cm.cnt;
+                va[w] = cm.first;
+            }
+            float e;
+            if (vc[w] == 0) {  // the X(t) cell above a stale bound, or nothing else left
+                if (!zin[w]) continue;
+                e = zv[w];
+                cnt[w] = 1;
+                arg[w] = pic[w];
+            } else if (zin[w] && zv[w] > vm[w]) {
+                e = zv[w];
+                cnt[w] = 1;
+                arg[w] = pic[w];
+            } else if (zin[w] && zv[w] == vm[w]) {
+                e = vm[w];
+                cnt[w] = vc[w] + 1;
+                arg[w] = min(va[w], pic[w]);
+            } else {
+                e = vm[w];
+                cnt[w] = vc[w];
+                arg[w] = va[w];
+            }
+            key[w] = fkey(e);
         }
-        int ties = 0;
-        for (int step = 0; step < n; ++step) {
-            if (step == depth && depth > 0) {
+        uint32_t lm = 0;
 #pragma unroll
-                for (int w = 0; w < NW; ++w)
-                    if (ckey[w]) col_scan<VT>(tile, rowdead, n, lane + 32 * w, pic[w], -1, ckey[w], ccnt[w]);
-            }
-            uint32_t lm = 0;
+        for (int w = 0; w < NW; ++w) lm = max(lm, key[w]);
+        const uint32_t gm = __reduce_max_sync(FULL, lm);
+        int lc = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) lm = ckey[w] > lm ? ckey[w] : lm;
-            const uint32_t gm = __reduce_max_sync(FULL, lm);
-            int lc = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) lc += (ckey[w] == gm) ? ccnt[w] : 0;
-            const int tot = (int)__reduce_add_sync(FULL, (unsigned)lc);
-            int k = 0;
-            if (tot > 1) {
-                ++ties;
-                if (s.tie_rule == 0) {
-                    const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
-                    k = (int)below(word_of(u, step & 3), (uint32_t)tot);
-                }
-            }
-            // the column holding the k-th element of M (columns j = lane + 32 w ascending)
-            int owner = -1, ow = 0, kk = 0;
+        for (int w = 0; w < NW; ++w) lc += (key[w] == gm) ? cnt[w] : 0;
+        const int tot = (int)__reduce_add_sync(FULL, (unsigned)lc);
+        // the column holding the k-th element of M (columns c = lane + 32 w ascending)
+        int owner = -1, ow = 0, kk = 0;
+        if (tot == 1) {
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 if (owner >= 0) continue;
-                const int c = (ckey[w] == gm) ? ccnt[w] : 0;
+                const unsigned bal = __ballot_sync(FULL, key[w] == gm);
+                if (bal) {
+                    owner = __ffs(bal) - 1;
+                    ow = w;
+                }
+            }
+        } else {
+            int k = 0;
+            ++ties;
+            if (s.tie_rule == 0) {
+                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                k = (int)below(word_of(u, step & 3), (uint32_t)tot);
+            }
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                if (owner >= 0) continue;
+                const int c = (key[w] == gm) ? cnt[w] : 0;
                 int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -277,50 +392,154 @@ __global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
                     k -= tw;
                 }
             }
-            // the owner lane finds the kk-th such row (ascending)
-            int r = -1;
-            const bool use_ex = step < depth;
-            if (lane == owner) {
+        }
+        // the owner takes the kk-th row (ascending) holding its column's maximum
+        int r = -1;
+        if (lane == owner) {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    if (w != ow) continue;
-                    const int col = lane + 32 * w;
-                    int seen = 0;
-                    for (int i = 0; i < n; ++i) {
-                        if (rowdead[i] || (use_ex && i == exrow[w])) continue;
-                        if (fkey(yval<NW, VT>(tile, n, i, col, pic[w])) == gm) {
-                            if (seen == kk) {
-                                r = i;
-                                break;
-                            }
-                            ++seen;
-                        }
-                    }
-                    newp[w] = r;
-                    ckey[w] = 0;
-                    ccnt[w] = 0;
+            for (int w = 0; w < NW; ++w) {
+                if (w != ow) continue;
+                r = arg[w];
+                if (kk > 0)  // several copies: the plain maximum, maybe tied with the X(t) cell
+                    r = kth_row<VT>(tile, dead, n, lane + 32 * w, pic[w], zin[w], zv[w], vm[w], kk);
+                newp[w] = r;
+                alive[w] = false;
+            }
+        }
+        r = __shfl_sync(FULL, r, owner < 0 ? 0 : owner);
+        if (owner < 0 || r < 0 || r >= n) {  // cannot happen; never index with it
+            if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            return ties;
+        }
+        if (lane == 0) dead[r >> 5] |= 1u << (r & 31);
+        __syncwarp();
+        // the other columns lose row r
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (!alive[w]) continue;
+            if (r == pic[w]) {
+                zal[w] = false;
+            } else if (vc[w] > 0 && VStore<VT>::to_f(tile[r * n + lane + 32 * w]) == vm[w]) {
+                if (--vc[w] > 0 && va[w] == r)
+                    va[w] = vnext<VT>(tile, dead, n, lane + 32 * w, pic[w], vm[w], r);
+            }
+        }
+        ++step;
+    }
+    return ties;
+}
+
+// Eq. 4 with S_v for one particle: reads V(t) from the tile, writes V(t+1) to global
+// memory and, when the position uses it (pos_uses_new_v), back into the tile. With
+// fp32 storage the unnormalised W is kept in the tile between the two passes.
+template <int NW, typename VT>
+__device__ __forceinline__ void velocity(const StateView& s, VT* tile, VT* Vg, int n, int lane, const int (&pic)[NW],
+                         const int (&plc)[NW], const int (&pgc)[NW], float a, float b, bool newv) {
+    const bool norm = s.sv_kind == 1;
+    constexpr bool kInPlace = sizeof(VT) == 4;
+    float sum[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sum[w] = 0.0f;
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int j = lane + 32 * w;
+            if (j < n) {
+                const float v = VStore<VT>::to_f(tile[i * n + j]);
+                const float dl = (float)((plc[w] == i) - (pic[w] == i));
+                const float dg = (float)((pgc[w] == i) - (pic[w] == i));
+                float x = fmaf(s.c1, v, a * dl + b * dg);
+                x = fminf(fmaxf(x, -s.v_max), s.v_max);
+                if (norm) {
+                    sum[w] += fabsf(x);
+                    if (kInPlace) tile[i * n + j] = VStore<VT>::from_f(x);
+                } else {
+                    const VT o = VStore<VT>::from_f(x);
+                    Vg[i * n + j] = o;
+                    if (newv) tile[i * n + j] = o;
                 }
             }
-            r = __shfl_sync(FULL, r, owner < 0 ? 0 : owner);
-            if (owner < 0 || r < 0 || r >= n) {  // cannot happen; never index with it
-                if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
-                break;
+        }
+    }
+    if (!norm) return;
+    float inv[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) inv[w] = sum[w] > 0.0f ? 1.0f / sum[w] : 1.0f;
+    for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int j = lane + 32 * w;
+            if (j < n) {
+                float x;
+                if (kInPlace) {
+                    x = VStore<VT>::to_f(tile[i * n + j]);
+                } else {
+                    const float v = VStore<VT>::to_f(tile[i * n + j]);
+                    const float dl = (float)((plc[w] == i) - (pic[w] == i));
+                    const float dg = (float)((pgc[w] == i) - (pic[w] == i));
+                    x = fmaf(s.c1, v, a * dl + b * dg);
+                    x = fminf(fmaxf(x, -s.v_max), s.v_max);
+                }
+                const VT o = VStore<VT>::from_f(x * inv[w]);
+                Vg[i * n + j] = o;
+                if (newv) tile[i * n + j] = o;
             }
-            if (lane == 0) rowdead[r] = 1;
+        }
+    }
+}
+
+template <int NW, typename VT>
+__global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
+    const int wpc = blockDim.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = s.n;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + warp;
+    unsigned char* wbase = smem + kBarBytes + warp * warp_bytes<VT>(n);
+    VT* tile = reinterpret_cast<VT*>(wbase);
+    uint32_t* dead = reinterpret_cast<uint32_t*>(wbase + tile_bytes<VT>(n));
+    const uint32_t t = (uint32_t)*s.t;
+    const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    uint32_t phase = 0;
+
+    for (int p = blockIdx.x * wpc + warp; p < s.P; p += gridDim.x * wpc) {
+        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+        // V(t) -> shared memory with one bulk copy (tile padded to 16 bytes)
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async();
+            bulk_load(tile, Vg, tbytes, bar);
+        }
+        int pic[NW], plc[NW], pgc[NW], newp[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int j = lane + 32 * w;
+            pic[w] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
+            plc[w] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
+            pgc[w] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+            newp[w] = 0;
+        }
+        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
+        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!__all_sync(FULL, ok)) {  // the copy never landed: record, leave this warp
+            if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            return;
+        }
+        const bool newv = s.pos_uses_new_v != 0;
+        int ties;
+        if (!newv) {  // Eq. 5 as printed: S_x on X(t) + V(t), then Eq. 4
+            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, newp);
             __syncwarp();
-            // columns whose maximum sat in row r lose one of its copies
-            if (!(step + 1 == depth)) {
-                const bool ex_next = step + 1 < depth;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    if (!ckey[w]) continue;
-                    if (ex_next && r == exrow[w]) continue;
-                    const uint32_t kr = fkey(yval<NW, VT>(tile, n, r, lane + 32 * w, pic[w]));
-                    if (kr == ckey[w] && --ccnt[w] == 0)
-                        col_scan<VT>(tile, rowdead, n, lane + 32 * w, pic[w], ex_next ? exrow[w] : -1,
-                                     ckey[w], ccnt[w]);
-                }
-            }
+            velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, false);
+        } else {
+            velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, true);
+            __syncwarp();
+            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, newp);
         }
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
@@ -334,22 +553,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
 
 template <int NW, typename VT>
 cudaError_t launch_vsx(const StateView& s, cudaStream_t st) {
-    const size_t smem = kWarps * warp_bytes<VT>(s.n);
-    int warps = kWarps;
+    int wpc = kWarps;  // warps (particles) per CTA, as many as shared memory allows
+    while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(s.n) > kSmemLimit) --wpc;
+    const size_t smem = kBarBytes + wpc * warp_bytes<VT>(s.n);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    (void)warps;
     cudaError_t e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_velocity_sx<NW, VT>, kWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_velocity_sx<NW, VT>, wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
-    const int need = (s.P + kWarps - 1) / kWarps;
+    const int need = (s.P + wpc - 1) / wpc;
     if (grid > need) grid = need;
-    k_velocity_sx<NW, VT><<<grid, kWarps * 32, smem, st>>>(s);
+    k_velocity_sx<NW, VT><<<grid, wpc * 32, smem, st>>>(s);
     return cudaGetLastError();
 }
 
@@ -361,8 +580,8 @@ cudaError_t launch_vsx_t(const StateView& s, cudaStream_t st) {
         case 3: return launch_vsx<3, VT>(s, st);
         case 4: return launch_vsx<4, VT>(s, st);
         case 5: return launch_vsx<5, VT>(s, st);
-        case 6: return launch_vsx<6, VT>(s, st);
-        case 7: return launch_vsx<7, VT>(s, st);
+        case 6:
+        case 7:
         case 8: return launch_vsx<8, VT>(s, st);
         default: return cudaErrorInvalidValue;
     }
@@ -372,7 +591,7 @@ cudaError_t launch_vsx_t(const StateView& s, cudaStream_t st) {
 
 int velocity_sx_max_n(int v_bf16) {
     int n = 2;
-    while (n < 256 && kWarps * (v_bf16 ? warp_bytes<__nv_bfloat16>(n + 1) : warp_bytes<float>(n + 1)) <=
+    while (n < 256 && kBarBytes + (v_bf16 ? warp_bytes<__nv_bfloat16>(n + 1) : warp_bytes<float>(n + 1)) <=
                           kSmemLimit)
         ++n;
     return n;

@@ -114,7 +114,7 @@ VARIANTS = {
 
 
 @pytest.mark.parametrize("variant", list(VARIANTS))
-@pytest.mark.parametrize("name,m,ss", [("tiny9", 2, 16), ("dense30", 3, 21), ("grid64", 4, 13)])
+@pytest.mark.parametrize("name,m,ss", [("tiny9", 3, 11), ("dense30", 3, 21), ("grid64", 4, 13)])
 def test_iterations_replay(Q, variant, name, m, ss):
     inst = INSTANCES[name]()
     kw = dict(swarms=m, swarm_size=ss)

@@ -198,6 +198,32 @@ int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds);
 
+/* ------------------------------------------------ allocation-free statistics */
+/* The same statistics as pso_stats (min, 5/25/50/75 % nearest-rank percentiles,
+ * max, mean), computed from `count` costs that the caller already holds in device
+ * memory, without allocating anything. This is for callers that cannot allocate
+ * device memory: for instance a serving loop that admits work against a fixed
+ * device-memory budget and must not see memory appear behind its back, or code
+ * that must not call cudaMalloc/cudaFree because those calls can synchronize the
+ * whole device. The paper has no counterpart; it exists for such callers.
+ *
+ * costs: device pointer, count int64 values, 1 <= count <= QAP_NOALLOC_MAX_COUNT
+ * (larger counts fail with QAP_ERR_INVALID_ARG). stream: cudaStream_t (NULL =
+ * legacy default stream). out6 and mean: host pointers receiving
+ * {min, p5, p25, p50, p75, max} and the mean; the call synchronizes `stream`.
+ *
+ * Scratch: one fixed device array inside this library (QAP_NOALLOC_MAX_COUNT
+ * int64 sort slots plus 8 result slots, 512 KiB + 64 B), held by every GPU that
+ * loads the library until the process exits. Each call rewrites every slot it
+ * reads, so nothing from an earlier call leaks into a result. All calls share
+ * the one array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller. The first call on a device
+ * looks up the array's device address once (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. */
+#define QAP_NOALLOC_MAX_COUNT 65536
+int qap_cost_stats_noalloc(const int64_t* costs, int32_t count, void* stream, int64_t* out6,
+                           double* mean);
+
 #ifdef __cplusplus
 }
 #endif

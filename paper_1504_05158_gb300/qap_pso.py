@@ -26,7 +26,9 @@ EXPORTS = [
     "qap_status_string", "qap_create_instance", "qap_destroy_instance", "qap_instance_info",
     "pso_params_default", "pso_init", "pso_step", "pso_step_timed", "pso_best", "pso_stats", "pso_destroy",
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
+    "qap_cost_stats_noalloc",
 ]
+NOALLOC_MAX_COUNT = 65536
 
 
 class QapError(RuntimeError):
@@ -109,6 +111,7 @@ def lib():
         L.pso_import_state.argtypes = [vp, C.POINTER(HostState)]
         L.qap_eval_costs.argtypes = [vp, vp, C.c_int32, vp]
         L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.qap_cost_stats_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -137,6 +140,19 @@ def default_params(**kw) -> Params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def cost_stats_noalloc(costs_dev_ptr, count, stream=None):
+    """Statistics of `count` int64 costs already in device memory, computed without
+    any device allocation (for callers that must not allocate; see the header).
+    Returns dict(min, p5, p25, p50, p75, max, mean)."""
+    out = np.zeros(6, np.int64)
+    mean = C.c_double()
+    st = C.c_void_p(stream) if stream else None
+    _check(lib().qap_cost_stats_noalloc(C.c_void_p(costs_dev_ptr), count, st, _ptr(out),
+                                        C.byref(mean)), "qap_cost_stats_noalloc")
+    return dict(min=int(out[0]), p5=int(out[1]), p25=int(out[2]), p50=int(out[3]),
+                p75=int(out[4]), max=int(out[5]), mean=mean.value)
 
 
 class Instance:

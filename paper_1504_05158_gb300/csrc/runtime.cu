@@ -20,6 +20,7 @@ struct qap_instance {
     int32_t max_f, max_d;
     int32_t exact32;
     int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
+    int32_t tc_exact;   // the tensor-core set-up of the local search is exact
 };
 
 struct pso_state {
@@ -99,6 +100,7 @@ LsArgs ls_args_for(const pso_state* s, bool init) {
     a.costL = s->sv.costL;
     a.counters = init ? nullptr : s->sv.counters;
     a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
+    a.tc_exact = s->inst->tc_exact;
     return a;
 }
 
@@ -164,6 +166,7 @@ int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_insta
     q->max_d = md;
     q->exact32 = ((long double)n * mf * md < (long double)(1 << 27)) ? 1 : 0;
     q->narrow_ok = md <= 65535 ? 1 : 0;
+    q->tc_exact = (sym && mf <= 2048 && md <= 2048 && (long double)n * mf * md < (long double)(1 << 24)) ? 1 : 0;
     const size_t bytes = (size_t)n * n * 4;
     cudaError_t e = cudaMalloc(&q->dF, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&q->dD, bytes);
@@ -608,6 +611,7 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
         a.moves = dm;
         a.rounds = dr;
         a.max_moves = max_moves;
+        a.tc_exact = inst->tc_exact;
         e = launch_ls(a, 0);
     }
     std::vector<int64_t> hc(count);

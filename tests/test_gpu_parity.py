@@ -233,3 +233,39 @@ def test_invalid_params(Q):
         with pytest.raises(Q.QapError) as e:
             Q.Swarm(gi, Q.default_params(**bad), seed=1)
         assert e.value.status == Q.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("setup", ["tc", "simt"])
+@pytest.mark.parametrize("name", ["n3", "tiny9", "dense30", "n33", "grid64"])
+def test_local_search_both_setups(Q, setup, name, monkeypatch):
+    # the tensor-core and SIMT set-ups of G give identical searches
+    if setup == "simt":
+        monkeypatch.setenv("QAP_PSO_LS_SETUP", "simt")
+    else:
+        monkeypatch.delenv("QAP_PSO_LS_SETUP", raising=False)
+    inst = INSTANCES[name]()
+    gi = Q.Instance(inst.F, inst.D)
+    perms = W.random_perms(37, inst.n, 17)
+    gp, gc, gm, gr = gi.local_search(perms, 0)
+    for i, p in enumerate(perms):
+        op, oc, om, orr, _ = O.local_search(inst.F, inst.D, p, 0)
+        assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om and gr[i] == orr, i
+    assert np.array_equal(gi.eval_costs(perms), [O.cost(inst.F, inst.D, p) for p in perms])
+
+
+def test_large_values_use_exact_simt_setup(Q):
+    # entries above 2048 leave the fp16 range: the SIMT set-up takes over, still exact
+    rng = np.random.default_rng(3)
+    n = 24
+    F = rng.integers(0, 5000, (n, n))
+    F = np.triu(F, 1)
+    F = (F + F.T).astype(np.int32)
+    D = rng.integers(0, 40, (n, n))
+    D = np.triu(D, 1)
+    D = (D + D.T).astype(np.int32)
+    gi = Q.Instance(F, D)
+    perms = W.random_perms(20, n, 4)
+    gp, gc, gm, gr = gi.local_search(perms, 0)
+    for i, p in enumerate(perms):
+        op, oc, om, orr, _ = O.local_search(F, D, p, 0)
+        assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om, i

@@ -15,12 +15,12 @@
 // so a round costs O(1) per pair after an O(n^3) set-up per iteration.
 //
 // The set-up G = F * D_p is a dense product. Two kernels form it:
-//   k_ls_tc (n <= 64, entries <= 2048, n max_f max_d < 2^24): on the tensor cores
-//     (tcgen05, fp16 operands, fp32 accumulation in tensor memory). Every operand
-//     and partial sum is an integer below 2^24, so the fp32 result is exact. With
-//     G[k][l] = sum_j' F[k][p^-1(j')] D[j'][l], the A operand is F with its columns
-//     gathered by p^-1 (per particle; 2 or 4 particles stacked to M = 128 rows) and
-//     the B operand is D itself (symmetric, shared by every particle).
+//   k_ls_team (n <= 64, symmetric, entries <= 2048, n max_f max_d < 2^24): on the
+//     tensor cores (tcgen05, fp16 operands, fp32 accumulation in tensor memory).
+//     Every operand and partial sum is an integer below 2^24, so the fp32 result is
+//     exact. With G[k][l] = sum_j' F[k][p^-1(j')] D[j'][l], the A operand is F with
+//     its columns gathered by p^-1 (one particle per M = 128 tile) and the B operand
+//     is D itself (symmetric, shared by every particle).
 //   k_ls (any n up to the shared-memory limit): integer multiply-adds on the SIMT
 //     cores.
 // Layout: F (int32, rows padded to fs) and D (uint16) are staged once per CTA in
@@ -202,7 +202,7 @@ __device__ __forceinline__ void store_cost_only(const LsArgs& a, int p, long lon
 // ------------------------------------------------------------ SIMT set-up
 template <int NW>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     const int n = a.n, fs = round_up(n, 4), gs = n + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t* sF = reinterpret_cast<int32_t*>(smem);
@@ -288,20 +288,25 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) 
 }
 
 // ------------------------------------------------------ tensor-core set-up
-// One CTA of 8 warps takes 8 particles at a time. R rows per particle (32 or 64)
-// stack 128 / R particles into one M = 128 tile; KP = NP = n rounded up to 16.
-struct TcLayout {
-    int n, R, KP, NP, tiles, fhs;
-    size_t oF, oD, oFh, oB, oPin, oGd, oPi, oBar, oT, oU, total;
+// Teams of WPP warps (WPP = 1 for n <= 32, 2 for n <= 64) search one particle at a
+// time, independently of the other teams of the CTA. A team's particle occupies the
+// rows of an M = 128 A tile that sit in the tensor-memory lane quarters of the
+// team's own warps (the other rows are never read back), the team has its own
+// tensor-memory columns and mbarrier, and particles come from a global counter, so
+// no team waits for another team's search. KP = NP = n rounded up to 16.
+template <int WPP>
+struct TeamLayout {
+    int n, KP, NP, fhs;
+    size_t oF, oD, oFh, oB, oPin, oGd, oPi, oX, oBar, oT, oU, ubytes, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int n) {
-    TcLayout L{};
+template <int WPP>
+__host__ __device__ inline TeamLayout<WPP> team_layout(int n) {
+    TeamLayout<WPP> L{};
+    constexpr int TEAMS = 8 / WPP;
     L.n = n;
-    L.R = n <= 32 ? 32 : 64;
     L.KP = round_up(n, 16);
     L.NP = L.KP;
-    L.tiles = 8 * L.R / 128;
     L.fhs = round_up(n, 4) + 2;  // odd word stride: column gathers free of bank conflicts
     size_t o = 0;
     auto take = [&](size_t b) {
@@ -313,35 +318,206 @@ __host__ __device__ inline TcLayout tc_layout(int n) {
     L.oD = take((size_t)n * n * 2);
     L.oFh = take((size_t)n * L.fhs * 2);
     L.oB = take((size_t)L.NP * L.KP * 2);
-    L.oPin = take(8 * 64);
-    L.oGd = take(8 * align16((size_t)n * 4));
-    L.oPi = take(8 * align16((size_t)n * 4));
-    L.oBar = take(16);
+    L.oPin = take(TEAMS * 64);
+    L.oGd = take(TEAMS * align16((size_t)n * 4));
+    L.oPi = take(TEAMS * align16((size_t)n * 4));
+    L.oX = take(TEAMS * 64);  // per team: next particle, reduction slots
+    L.oBar = take(TEAMS * 8);
     L.oT = take(16);
-    const size_t a_bytes = (size_t)L.tiles * 128 * L.KP * 2;
-    const size_t gbytes = 8 * g_bytes(n);
-    L.oU = take(a_bytes > gbytes ? a_bytes : gbytes);
+    const size_t a_bytes = (size_t)128 * L.KP * 2;
+    L.ubytes = (a_bytes > g_bytes(n) ? a_bytes : g_bytes(n) + 127) & ~size_t(127);
+    L.oU = take((size_t)TEAMS * L.ubytes);
     L.total = o;
     return L;
 }
 
-template <int NW>
-__global__ void __launch_bounds__(256) k_ls_tc(LsArgs a) {
+template <int WPP>
+__device__ __forceinline__ void team_sync(int team) {
+    if (WPP == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * WPP) : "memory");
+}
+
+// true on every thread of the team iff v is true on every thread of the team
+template <int WPP>
+__device__ __forceinline__ bool team_all(bool v, int team) {
+    if (WPP == 1) return __all_sync(FULL, v);
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, %2, %3, pi;\n"
+        " selp.u32 %0, 1, 0, po;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + team), "r"(32 * WPP)
+        : "memory");
+    return r != 0;
+}
+
+// team-wide lexicographic minimum of (value, key); xch: 2 x WPP x 2 ints, used
+// alternately (`parity`) so consecutive reductions need a single barrier each
+template <int WPP>
+__device__ __forceinline__ void team_min2(int& v, unsigned& key, int* xch, int parity, int team, int lane,
+                                          int wi) {
+    const int mv = __reduce_min_sync(FULL, v);
+    const unsigned mk = __reduce_min_sync(FULL, v == mv ? key : 0xFFFFFFFFu);
+    if (WPP == 1) {
+        v = mv;
+        key = mk;
+        return;
+    }
+    int* x = xch + parity * 2 * WPP;
+    if (lane == 0) {
+        x[2 * wi] = mv;
+        x[2 * wi + 1] = (int)mk;
+    }
+    team_sync<WPP>(team);
+    int bv = x[0];
+    unsigned bk = (unsigned)x[1];
+#pragma unroll
+    for (int w = 1; w < WPP; ++w) {
+        const int ov = x[2 * w];
+        const unsigned ok = (unsigned)x[2 * w + 1];
+        if (ov < bv || (ov == bv && ok < bk)) {
+            bv = ov;
+            bk = ok;
+        }
+    }
+    v = bv;
+    key = bk;
+}
+
+template <int WPP>
+__device__ __forceinline__ long long team_sum64(long long v, long long* xch, int team, int lane, int wi) {
+    v = warp_sum64(v);
+    if (WPP == 1) return v;
+    if (lane == 0) xch[wi] = v;
+    team_sync<WPP>(team);
+    long long t = 0;
+#pragma unroll
+    for (int w = 0; w < WPP; ++w) t += xch[w];
+    team_sync<WPP>(team);
+    return t;
+}
+
+// Best-improvement descent of particle p by one team from a complete G: thread tt
+// owns pair slot e = tt of every virtual row and column l = tt of G.
+template <int WPP>
+__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32_t* sF, const uint16_t* sD,
+                                             int32_t* G, int32_t* gd, int32_t* pi, int* xch, int tt,
+                                             int team) {
+    constexpr int TT = 32 * WPP;
+    const int n = a.n, fs = round_up(n, 4), gs = n + 1;
+    const int lane = tt & 31, wi = tt >> 5;
+    const long long npairs = (long long)n * (n - 1) / 2;
+    const int nv = n / 2;
+    long long part = 0;
+    for (int m = tt; m < n; m += TT) {
+        gd[m] = G[m * gs + pi[m]];
+        part += gd[m];
+    }
+    long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch + 8), team, lane, wi);
+    int moves = 0, rounds = 0;
+    if (a.max_moves >= 0) {
+        for (;;) {
+            if (a.max_moves > 0 && moves >= a.max_moves) break;
+            if (moves >= kSafetyMoves) {
+                if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            int best = INT_MAX;
+            unsigned bkey = 0xFFFFFFFFu;
+            const int e = tt;
+            if (e < n) {
+                for (int t = 0; t < nv; ++t) {
+                    int k, m;
+                    if (e < n - 1 - t) {
+                        k = t;
+                        m = t + 1 + e;
+                    } else {
+                        k = n - 2 - t;
+                        m = e;
+                        if (k == t) continue;
+                    }
+                    const int pk = pi[k], pmm = pi[m];
+                    const int d = 2 * (G[k * gs + pmm] + G[m * gs + pk] - gd[k] - gd[m]) +
+                                  4 * sF[k * fs + m] * (int)sD[pk * n + pmm];
+                    const unsigned key = ((unsigned)k << 8) | (unsigned)m;
+                    if (d < best || (d == best && key < bkey)) {
+                        best = d;
+                        bkey = key;
+                    }
+                }
+            }
+            team_min2<WPP>(best, bkey, xch, rounds & 1, team, lane, wi);
+            ++rounds;
+            if (best >= 0) break;
+            const int r = (int)(bkey >> 8), s = (int)(bkey & 255u);
+            if (r >= n || s >= n || r >= s) {  // cannot happen; never index with it
+                if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            const int pr = pi[r], pss = pi[s];
+            if (tt < n) {
+                const int bt = (int)sD[pss * n + tt] - (int)sD[pr * n + tt];
+                for (int k = 0; k < n; ++k) G[k * gs + tt] += (sF[r * fs + k] - sF[s * fs + k]) * bt;
+            }
+            team_sync<WPP>(team);  // G complete; p itself is still the old one
+            for (int m = tt; m < n; m += TT) {
+                const int pm = m == r ? pss : (m == s ? pr : pi[m]);
+                gd[m] = G[m * gs + pm];
+                if (m == r || m == s) pi[m] = pm;
+            }
+            team_sync<WPP>(team);
+            cost += best;
+            ++moves;
+        }
+    }
+    for (int m = tt; m < n; m += TT) a.out[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+    if (a.PL) {
+        const long long old = a.costL[p];
+        if (cost < old) {
+            for (int m = tt; m < n; m += TT) a.PL[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+            if (tt == 0) a.costL[p] = cost;
+        }
+    }
+    if (tt == 0) {
+        a.cost[p] = cost;
+        if (a.moves) a.moves[p] = moves;
+        if (a.rounds) a.rounds[p] = rounds;
+        if (a.counters) {
+            atomicAdd(a.counters + CNT_PIT, 1ull);
+            if (a.max_moves >= 0) {
+                atomicAdd(a.counters + CNT_MOVES, (unsigned long long)moves);
+                atomicAdd(a.counters + CNT_ROUNDS, (unsigned long long)rounds);
+                if (rounds > 0) {
+                    atomicAdd(a.counters + CNT_DELTA_FULL, (unsigned long long)npairs);
+                    atomicAdd(a.counters + CNT_DELTA_INCR, (unsigned long long)((rounds - 1) * npairs));
+                }
+            }
+        }
+    }
+}
+
+template <int WPP>
+__global__ void __launch_bounds__(256) k_ls_team(LsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int TT = 32 * WPP, TEAMS = 8 / WPP;
     const int n = a.n, fs = round_up(n, 4);
-    const TcLayout L = tc_layout(n);
+    const TeamLayout<WPP> L = team_layout<WPP>(n);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int team = warp / WPP, tt = tid - team * TT;
     int32_t* sF = reinterpret_cast<int32_t*>(smem + L.oF);
     uint16_t* sD = reinterpret_cast<uint16_t*>(smem + L.oD);
     __half* sFh = reinterpret_cast<__half*>(smem + L.oFh);
     unsigned char* sB = smem + L.oB;
-    uint8_t* pinv = smem + L.oPin;
-    int32_t* gd = reinterpret_cast<int32_t*>(smem + L.oGd + warp * align16((size_t)n * 4));
-    int32_t* pi = reinterpret_cast<int32_t*>(smem + L.oPi + warp * align16((size_t)n * 4));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.oBar);
+    uint8_t* pinv = smem + L.oPin + team * 64;
+    int32_t* gd = reinterpret_cast<int32_t*>(smem + L.oGd + team * align16((size_t)n * 4));
+    int32_t* pi = reinterpret_cast<int32_t*>(smem + L.oPi + team * align16((size_t)n * 4));
+    int* xch = reinterpret_cast<int*>(smem + L.oX + team * 64);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.oBar) + team;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.oT);
-    unsigned char* U = smem + L.oU;
-    int32_t* G = reinterpret_cast<int32_t*>(U + warp * g_bytes(n));
+    unsigned char* U = smem + L.oU + (size_t)team * L.ubytes;
+    int32_t* G = reinterpret_cast<int32_t*>(U);
 
     stage_fd(a, sF, sD, fs);
     for (int i = tid; i < n * L.fhs; i += blockDim.x) {
@@ -355,103 +531,93 @@ __global__ void __launch_bounds__(256) k_ls_tc(LsArgs a) {
         *reinterpret_cast<__half*>(sB + tc::tile_offset(l, j, L.KP)) = __int2half_rn(v);
     }
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(L.tiles * L.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)(TEAMS * L.NP)) ncols <<= 1;
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
-    if (tid == 0) mbar_init(bar, 1);
+    if (tt == 0) mbar_init(bar, 1);
     fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tbase = *tslot;
+    const uint32_t tcol = *tslot + (uint32_t)(team * L.NP);
     const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
     const uint32_t sbo = (uint32_t)(L.KP / 8) * 128;
+    const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
+    const int wq = warp & 3;                      // this warp's lane quarter
     uint32_t phase = 0;
-    bool healthy = true;
-    const int groups = (a.count + 7) / 8;
+    int next = blockIdx.x * TEAMS + team;
+    const int stride = gridDim.x * TEAMS;
 
-    for (int g = blockIdx.x; g < groups && healthy; g += gridDim.x) {
-        const int p = g * 8 + warp;
-        const bool mine = p < a.count;
-        // positions and their inverses
-        for (int m = lane; m < n; m += 32) {
-            const int v = mine ? a.in[(size_t)p * a.ps_in + m] : m;
-            pi[m] = v;
-            pinv[warp * 64 + v] = (uint8_t)m;
+    for (;;) {
+        int p;
+        if (a.work) {
+            if (tt == 0) xch[15] = atomicAdd(a.work, 1);
+            team_sync<WPP>(team);
+            p = xch[15];
+            team_sync<WPP>(team);
+        } else {
+            p = next;
+            next += stride;
         }
-        __syncthreads();
-        // A operands: tile T row r is particle q = T * (128 / R) + r / R, facility k =
-        // r % R; column j' holds F[k][p_q^-1(j')]
-        const int rows = L.tiles * 128;
-        for (int row = tid; row < rows; row += blockDim.x) {
-            const int T = row >> 7, r = row & 127;
-            const int q = T * (128 / L.R) + r / L.R, k = r % L.R;
-            unsigned char* At = U + (size_t)T * 128 * L.KP * 2;
-            const uint8_t* inv = pinv + q * 64;
+        if (p >= a.count) break;
+        for (int m = tt; m < n; m += TT) {
+            const int v = a.in[(size_t)p * a.ps_in + m];
+            pi[m] = v;
+            pinv[v] = (uint8_t)m;
+        }
+        team_sync<WPP>(team);
+        // A rows of this particle: row rowbase + k holds F[k][p^-1(j')] in column j'
+        for (int k = tt; k < n; k += TT) {
             for (int c = 0; c < L.KP; c += 8) {
                 __align__(16) __half h[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int j = c + e;
-                    h[e] = (k < n && j < n) ? sFh[k * L.fhs + inv[j]] : __int2half_rn(0);
+                    h[e] = j < n ? sFh[k * L.fhs + pinv[j]] : __int2half_rn(0);
                 }
-                *reinterpret_cast<uint4*>(At + tc::tile_offset(r, c, L.KP)) = *reinterpret_cast<uint4*>(h);
+                *reinterpret_cast<uint4*>(U + tc::tile_offset(rowbase + k, c, L.KP)) =
+                    *reinterpret_cast<uint4*>(h);
             }
         }
         fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
+        team_sync<WPP>(team);
+        if (tt == 0) {
             tc::fence_after_sync();
-            const uint32_t b0 = smem_u32(sB);
-            for (int T = 0; T < L.tiles; ++T) {
-                const uint32_t a0 = smem_u32(U + (size_t)T * 128 * L.KP * 2);
-                for (int s = 0; s < L.KP / 16; ++s)
-                    tc::mma_f16(tbase + (uint32_t)(T * L.NP), tc::smem_desc(a0 + s * 256, 128, sbo),
-                                tc::smem_desc(b0 + s * 256, 128, sbo), idesc, s > 0);
-            }
+            const uint32_t a0 = smem_u32(U), b0 = smem_u32(sB);
+            for (int s = 0; s < L.KP / 16; ++s)
+                tc::mma_f16(tcol, tc::smem_desc(a0 + s * 256, 128, sbo), tc::smem_desc(b0 + s * 256, 128, sbo),
+                            idesc, s > 0);
             tc::mma_commit(bar);
         }
-        const bool ok = mbar_wait(bar, phase);
+        const bool ok = team_all<WPP>(mbar_wait(bar, phase), team);
         phase ^= 1u;
-        if (!__syncthreads_and(ok)) {  // the products never completed: record and stop
-            if (tid == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
-            healthy = false;
+        if (!ok) {  // the product never completed: record and leave (cannot be expected)
+            if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
             break;
         }
         tc::fence_after_sync();
-        // G from tensor memory: warp w reads lane quarter w % 4 of tiles w/4, w/4 + 2, ...
-        for (int T = warp >> 2; T < L.tiles; T += 2) {
-            const int r = 32 * (warp & 3) + lane;
-            const int q = T * (128 / L.R) + r / L.R, k = r % L.R;
-            int32_t* Gq = reinterpret_cast<int32_t*>(U + (size_t)q * g_bytes(n));
-            const bool valid = k < n && g * 8 + q < a.count;
+        // G from tensor memory: this warp's quarter holds rows k = 32 (warp % WPP) + lane
+        {
+            const int k = 32 * (warp % WPP) + lane;
             for (int c = 0; c < L.NP; c += 16) {
                 uint32_t v[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(T * L.NP + c), v);
+                tc::tmem_ld16(tcol + ((uint32_t)(32 * wq) << 16) + (uint32_t)c, v);
                 tc::tmem_wait_ld();
-                // G region overlaps the A tiles, which the finished products no longer read
-                if (valid) {
+                // G overwrites the A tile, which the completed product no longer reads
+                if (k < n) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
-                        if (c + e < n) Gq[k * (n + 1) + c + e] = __float2int_rn(__uint_as_float(v[e]));
+                        if (c + e < n) G[k * (n + 1) + c + e] = __float2int_rn(__uint_as_float(v[e]));
                 }
             }
         }
         tc::fence_before_sync();
-        __syncthreads();
-        if (mine) {
-            if (a.max_moves < 0) {
-                long long part = 0;
-                for (int m = lane; m < n; m += 32) part += G[m * (n + 1) + pi[m]];
-                store_cost_only(a, p, warp_sum64(part), pi, lane);
-            } else {
-                descend_and_store<NW>(a, p, sF, sD, G, gd, pi, lane);
-            }
-        }
-        __syncthreads();
+        team_sync<WPP>(team);
+        descend_team<WPP>(a, p, sF, sD, G, gd, pi, xch, tt, team);
+        team_sync<WPP>(team);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+    if (warp == 0) tc::tmem_dealloc(*tslot, ncols);
 }
 
 bool use_tensor_cores(const LsArgs& a) {
@@ -460,28 +626,40 @@ bool use_tensor_cores(const LsArgs& a) {
     return !(env && strcmp(env, "simt") == 0);
 }
 
-template <int NW>
-cudaError_t launch_tc(const LsArgs& a, cudaStream_t st) {
-    const TcLayout L = tc_layout(a.n);
+template <int WPP>
+cudaError_t launch_team(const LsArgs& a, cudaStream_t st) {
+    const TeamLayout<WPP> L = team_layout<WPP>(a.n);
     if (L.total > kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_ls_tc<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)L.total);
+    // all of the unified L1 / shared storage as shared memory, so two CTAs fit an SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls_tc<NW>, 256, L.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls_team<WPP>, 256, L.total);
+    int smem_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int by_smem = smem_sm / (int)(L.total + reserved);
+    if (by_smem > per_sm) per_sm = by_smem;  // the occupancy query can ignore the carveout request
     // co-resident CTAs must fit the 512 tensor-memory columns together
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(L.tiles * L.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)((8 / WPP) * L.NP)) ncols <<= 1;
     const int tmem_cap = (int)(512 / ncols);
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
-    const int need = (a.count + 7) / 8;
+    const int need = (a.count + (8 / WPP) - 1) / (8 / WPP);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_ls_tc<NW><<<grid, 256, L.total, st>>>(a);
+    if (a.work) {
+        e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_ls_team<WPP><<<grid, 256, L.total, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -494,6 +672,8 @@ cudaError_t launch_nw(const LsArgs& a, cudaStream_t st) {
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_ls<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ls<NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -519,7 +699,7 @@ int ls_max_n() {
 cudaError_t launch_ls(const LsArgs& a, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     if (a.n < 2 || a.n > ls_max_n()) return cudaErrorInvalidValue;
-    if (use_tensor_cores(a)) return a.n <= 32 ? launch_tc<1>(a, st) : launch_tc<2>(a, st);
+    if (use_tensor_cores(a)) return a.n <= 32 ? launch_team<1>(a, st) : launch_team<2>(a, st);
     switch ((a.n + 31) / 32) {
         case 1: return launch_nw<1>(a, st);
         case 2: return launch_nw<2>(a, st);

@@ -559,6 +559,8 @@ cudaError_t launch_vsx(const StateView& s, cudaStream_t st) {
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

@@ -26,6 +26,7 @@ struct LsArgs {
     int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
     int32_t tc_exact;  // symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
                        // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT)
+    int32_t* work;     // device counter handing out particles (zeroed per launch), may be null
 };
 
 // Largest n the local search supports (one warp's G matrix in shared memory).

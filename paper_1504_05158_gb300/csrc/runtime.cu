@@ -34,6 +34,7 @@ struct pso_state {
     int64_t* stats_buf;
     int32_t stats_len;
     int64_t* stats_out;  // 6 int64 + 1 double
+    int32_t* work;       // particle counter of the local-search kernel
     cudaGraphExec_t g1, g16;
 };
 
@@ -101,6 +102,7 @@ LsArgs ls_args_for(const pso_state* s, bool init) {
     a.counters = init ? nullptr : s->sv.counters;
     a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
     a.tc_exact = s->inst->tc_exact;
+    a.work = s->work;
     return a;
 }
 
@@ -271,6 +273,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     const size_t ocostG = take((size_t)m * 8), ocostG2 = take((size_t)m * 8);
     const size_t obest = take(sv.ps), obc = take(8), obi = take(4), ot = take(4);
     const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
+    const size_t owork = take(4);
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -298,6 +301,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     sv.counters = (unsigned long long*)(base + ocnt);
     s->stats_buf = (int64_t*)(base + ostb);
     s->stats_out = (int64_t*)(base + osto);
+    s->work = (int32_t*)(base + owork);
     sv.seed = seed;
     sv.c1 = params->c1;
     sv.c2 = params->c2;
@@ -591,8 +595,9 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
         for (int j = 0; j < n; ++j) hp[(size_t)c * ps + j] = (uint8_t)perms[(size_t)c * n + j];
     uint8_t *din = nullptr, *dout = nullptr;
     int64_t* dc = nullptr;
-    int32_t *dm = nullptr, *dr = nullptr;
+    int32_t *dm = nullptr, *dr = nullptr, *dw = nullptr;
     cudaError_t e = cudaMalloc(&din, hp.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dw, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&dout, hp.size());
     if (e == cudaSuccess) e = cudaMalloc(&dc, (size_t)count * 8);
     if (e == cudaSuccess) e = cudaMalloc(&dm, (size_t)count * 4);
@@ -612,6 +617,7 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
         a.rounds = dr;
         a.max_moves = max_moves;
         a.tc_exact = inst->tc_exact;
+        a.work = dw;
         e = launch_ls(a, 0);
     }
     std::vector<int64_t> hc(count);
@@ -626,6 +632,7 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
     cudaFree(dc);
     cudaFree(dm);
     cudaFree(dr);
+    cudaFree(dw);
     if (e != cudaSuccess) return status_of(e);
     for (int c = 0; c < count; ++c) {
         if (perms_out)

@@ -185,6 +185,33 @@ int pso_export_state(pso_state_t st, pso_host_state_t* out);
  * storage format; X_sx and moves are ignored). Synchronises. */
 int pso_import_state(pso_state_t st, const pso_host_state_t* in);
 
+/* ---------------------------------------------------------------- batches */
+/* Many independent populations advanced together, e.g. many QAP instances of
+ * different n (the multi-swarm method of section 3 applied to each). Every phase
+ * of an iteration runs as one kernel launch over all members (the local search
+ * as one launch per kernel kind present: tensor-core set-up for n <= 64 with small
+ * entries, SIMT set-up otherwise); iterations are replayed from a captured CUDA
+ * graph. Results of every member are identical to running it alone. */
+typedef struct pso_batch* pso_batch_t;
+
+/* insts, params, seeds: `count` entries each; every member must use the same
+ * v_storage. stream as in pso_init (shared by all members). autotune != 0 times
+ * candidate launch shapes on the batch's own data (cached per process by shape),
+ * then re-initialises every member from its seed, so tuning never changes
+ * results. Errors as pso_init for any member. */
+int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_params_t* params,
+                     const uint64_t* seeds, void* stream, int32_t autotune, pso_batch_t* out);
+/* Queues `iterations` iterations of every member (asynchronous). */
+int pso_batch_step(pso_batch_t b, int32_t iterations);
+/* As pso_step_timed, over the whole batch (ms_out[1] covers every search launch). */
+int pso_batch_step_timed(pso_batch_t b, int32_t iterations, void* flush_buf, size_t flush_bytes,
+                         float* ms_out);
+int pso_batch_size(pso_batch_t b, int32_t* count);
+/* Borrowed handle of member `index` for pso_best, pso_stats, pso_export_state and
+ * pso_import_state; it stays owned by the batch (never pso_destroy it). */
+int pso_batch_member(pso_batch_t b, int32_t index, pso_state_t* out);
+void pso_batch_destroy(pso_batch_t b);
+
 /* ------------------------------------------------ single-kernel entry points */
 /* Goal function (Eq. 1) of `count` permutations (host, count x n int32) on the
  * device; out: count int64. */

@@ -25,8 +25,10 @@ __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, int 
     for (int i = lane; i < n; i += 32) dst[i] = src[i];
 }
 
-__global__ void __launch_bounds__(kThreads) k_bests(StateView s, int init_mode) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// one CTA per population of the table
+__global__ void __launch_bounds__(kThreads) k_bests(const StateView* __restrict__ views, int init_mode) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const StateView s = views[blockIdx.x];
     const int m = s.m, ss = s.ss, n = s.n;
     long long* sb_cost = reinterpret_cast<long long*>(smem);
     int* sb_idx = reinterpret_cast<int*>(sb_cost + m);
@@ -185,15 +187,16 @@ __global__ void __launch_bounds__(kThreads) k_stats(const int64_t* cost, int cou
 
 int bests_max_swarms() { return kMaxSwarms; }
 
-cudaError_t launch_bests(const StateView& s, int init_mode, cudaStream_t st) {
-    if (s.m > kMaxSwarms) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)s.m * (8 + 4 + 4);
+cudaError_t launch_bests(const StateView* d_views, int count, int m_max, int init_mode, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (m_max > kMaxSwarms) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)m_max * (8 + 4 + 4);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_bests, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_bests<<<1, kThreads, smem, st>>>(s, init_mode);
+    k_bests<<<count, kThreads, smem, st>>>(d_views, init_mode);
     return cudaGetLastError();
 }
 

@@ -200,9 +200,13 @@ __device__ __forceinline__ void store_cost_only(const LsArgs& a, int p, long lon
 }
 
 // ------------------------------------------------------------ SIMT set-up
+// cpi CTAs per population of the table: CTA b serves population b / cpi
 template <int NW>
-__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) {
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __restrict__ args, int cpi,
+                                                             int wpc) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    const LsArgs a = args[blockIdx.x / cpi];
+    const int cb = blockIdx.x % cpi;
     const int n = a.n, fs = round_up(n, 4), gs = n + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t* sF = reinterpret_cast<int32_t*>(smem);
@@ -216,8 +220,17 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) 
     __syncthreads();
     if (warp >= wpc) return;
 
-    for (int p = blockIdx.x * wpc + warp; p < a.count; p += gridDim.x * wpc) {
-        for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)p * a.ps_in + m];
+    int p = cb * wpc + warp;
+    for (;;) {
+        if (a.work) {
+            int q = 0;
+            if (lane == 0) q = atomicAdd(a.work, 1);
+            p = __shfl_sync(FULL, q, 0);
+        }
+        if (p >= a.count) break;
+        const int pcur = p;
+        if (!a.work) p += cpi * wpc;
+        for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)pcur * a.ps_in + m];
         __syncwarp();
         int pm[NW];
 #pragma unroll
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) 
                     part += col;
                 }
             }
-            store_cost_only(a, p, warp_sum64(part), pi, lane);
+            store_cost_only(a, pcur, warp_sum64(part), pi, lane);
             continue;
         }
         // ---- set-up: G = F * D_p (rows of D gathered by p) ----
@@ -283,7 +296,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(LsArgs a, int wpc) 
             }
         }
         __syncwarp();
-        descend_and_store<NW>(a, p, sF, sD, G, gd, pi, lane);
+        descend_and_store<NW>(a, pcur, sF, sD, G, gd, pi, lane);
     }
 }
 
@@ -498,10 +511,13 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32
     }
 }
 
+// cpi CTAs per population of the table: CTA b serves population b / cpi
 template <int WPP>
-__global__ void __launch_bounds__(256) k_ls_team(LsArgs a) {
+__global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args, int cpi) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int TT = 32 * WPP, TEAMS = 8 / WPP;
+    const LsArgs a = args[blockIdx.x / cpi];
+    const int cb = blockIdx.x % cpi;
     const int n = a.n, fs = round_up(n, 4);
     const TeamLayout<WPP> L = team_layout<WPP>(n);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -544,8 +560,8 @@ __global__ void __launch_bounds__(256) k_ls_team(LsArgs a) {
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
     const int wq = warp & 3;                      // this warp's lane quarter
     uint32_t phase = 0;
-    int next = blockIdx.x * TEAMS + team;
-    const int stride = gridDim.x * TEAMS;
+    int next = cb * TEAMS + team;
+    const int stride = cpi * TEAMS;
 
     for (;;) {
         int p;
@@ -620,18 +636,12 @@ __global__ void __launch_bounds__(256) k_ls_team(LsArgs a) {
     if (warp == 0) tc::tmem_dealloc(*tslot, ncols);
 }
 
-bool use_tensor_cores(const LsArgs& a) {
-    if (!a.tc_exact || a.n > 64) return false;
-    const char* env = getenv("QAP_PSO_LS_SETUP");
-    return !(env && strcmp(env, "simt") == 0);
-}
-
 template <int WPP>
-cudaError_t launch_team(const LsArgs& a, cudaStream_t st) {
-    const TeamLayout<WPP> L = team_layout<WPP>(a.n);
-    if (L.total > kSmemLimit) return cudaErrorInvalidValue;
+cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
+    const TeamLayout<WPP> T = team_layout<WPP>(L.n_max);
+    if (T.total > kSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L.total);
+                                         (int)T.total);
     // all of the unified L1 / shared storage as shared memory, so two CTAs fit an SM
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -639,33 +649,34 @@ cudaError_t launch_team(const LsArgs& a, cudaStream_t st) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls_team<WPP>, 256, L.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls_team<WPP>, 256, T.total);
     int smem_sm = 0, reserved = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    const int by_smem = smem_sm / (int)(L.total + reserved);
+    const int by_smem = smem_sm / (int)(T.total + reserved);
     if (by_smem > per_sm) per_sm = by_smem;  // the occupancy query can ignore the carveout request
     // co-resident CTAs must fit the 512 tensor-memory columns together
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)((8 / WPP) * L.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)((8 / WPP) * T.NP)) ncols <<= 1;
     const int tmem_cap = (int)(512 / ncols);
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     if (per_sm < 1) per_sm = 1;
-    int grid = sms * per_sm;
-    const int need = (a.count + (8 / WPP) - 1) / (8 / WPP);
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    if (a.work) {
-        e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
-        if (e != cudaSuccess) return e;
+    int cpi = L.cpi;
+    if (cpi <= 0) {  // one wave over the table, at least one CTA per population
+        cpi = (sms * per_sm + L.count - 1) / L.count;
+        const int per_pop = (L.total / L.count + (8 / WPP) - 1) / (8 / WPP);
+        if (cpi > per_pop) cpi = per_pop;
+        if (cpi < 1) cpi = 1;
     }
-    k_ls_team<WPP><<<grid, 256, L.total, st>>>(a);
+    e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
+    if (e != cudaSuccess) return e;
+    k_ls_team<WPP><<<L.count * cpi, 256, T.total, st>>>(L.d_args, cpi);
     return cudaGetLastError();
 }
 
 template <int NW>
-cudaError_t launch_nw(const LsArgs& a, cudaStream_t st) {
-    const int n = a.n;
+cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
+    const int n = L.n_max;
     int wpc = kMaxWarpsPerCta;
     while (wpc > 1 && shared_part(n) + wpc * warp_part(n) > kSmemLimit) --wpc;
     const size_t smem = shared_part(n) + wpc * warp_part(n);
@@ -680,11 +691,16 @@ cudaError_t launch_nw(const LsArgs& a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls<NW>, wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
-    int grid = sms * per_sm;
-    const int need = (a.count + wpc - 1) / wpc;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    k_ls<NW><<<grid, wpc * 32, smem, st>>>(a, wpc);
+    int cpi = L.cpi;
+    if (cpi <= 0) {
+        cpi = (sms * per_sm + L.count - 1) / L.count;
+        const int per_pop = (L.total / L.count + wpc - 1) / wpc;
+        if (cpi > per_pop) cpi = per_pop;
+        if (cpi < 1) cpi = 1;
+    }
+    e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
+    if (e != cudaSuccess) return e;
+    k_ls<NW><<<L.count * cpi, wpc * 32, smem, st>>>(L.d_args, cpi, wpc);
     return cudaGetLastError();
 }
 
@@ -696,16 +712,24 @@ int ls_max_n() {
     return n < 160 ? n : 160;
 }
 
-cudaError_t launch_ls(const LsArgs& a, cudaStream_t st) {
-    if (a.count <= 0) return cudaSuccess;
-    if (a.n < 2 || a.n > ls_max_n()) return cudaErrorInvalidValue;
-    if (use_tensor_cores(a)) return a.n <= 32 ? launch_team<1>(a, st) : launch_team<2>(a, st);
-    switch ((a.n + 31) / 32) {
-        case 1: return launch_nw<1>(a, st);
-        case 2: return launch_nw<2>(a, st);
-        case 3: return launch_nw<3>(a, st);
-        case 4: return launch_nw<4>(a, st);
-        case 5: return launch_nw<5>(a, st);
+LsKind ls_kind(const LsArgs& a) {
+    const char* env = getenv("QAP_PSO_LS_SETUP");
+    const bool simt = env && strcmp(env, "simt") == 0;
+    if (!a.tc_exact || a.n > 64 || simt) return LS_SIMT;
+    return a.n <= 32 ? LS_TEAM1 : LS_TEAM2;
+}
+
+cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
+    if (L.count <= 0 || L.total <= 0) return cudaSuccess;
+    if (L.n_max < 2 || L.n_max > ls_max_n()) return cudaErrorInvalidValue;
+    if (L.kind == LS_TEAM1) return launch_team<1>(L, st);
+    if (L.kind == LS_TEAM2) return launch_team<2>(L, st);
+    switch ((L.n_max + 31) / 32) {
+        case 1: return launch_nw<1>(L, st);
+        case 2: return launch_nw<2>(L, st);
+        case 3: return launch_nw<3>(L, st);
+        case 4: return launch_nw<4>(L, st);
+        case 5: return launch_nw<5>(L, st);
         default: return cudaErrorInvalidValue;
     }
 }

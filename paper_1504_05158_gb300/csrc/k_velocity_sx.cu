@@ -488,23 +488,32 @@ __device__ __forceinline__ void velocity(const StateView& s, VT* tile, VT* Vg, i
     }
 }
 
+// Covers a table of populations: flat particle index f over all of them (prefix
+// offsets), shared-memory slots sized for the largest n of the table.
 template <int NW, typename VT>
-__global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
+__global__ void __launch_bounds__(kWarps * 32)
+    k_velocity_sx(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count,
+                  int n_max) {
     const int wpc = blockDim.x >> 5;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = s.n;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + warp;
-    unsigned char* wbase = smem + kBarBytes + warp * warp_bytes<VT>(n);
+    unsigned char* wbase = smem + kBarBytes + warp * warp_bytes<VT>(n_max);
     VT* tile = reinterpret_cast<VT*>(wbase);
-    uint32_t* dead = reinterpret_cast<uint32_t*>(wbase + tile_bytes<VT>(n));
-    const uint32_t t = (uint32_t)*s.t;
-    const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
+    uint32_t* dead = reinterpret_cast<uint32_t*>(wbase + tile_bytes<VT>(n_max));
     if (lane == 0) mbar_init(bar, 1);
     __syncwarp();
     uint32_t phase = 0;
+    const int total = prefix[count];
+    int inst = 0;
 
-    for (int p = blockIdx.x * wpc + warp; p < s.P; p += gridDim.x * wpc) {
+    for (int f = blockIdx.x * wpc + warp; f < total; f += gridDim.x * wpc) {
+        while (inst + 1 < count && prefix[inst + 1] <= f) ++inst;  // f only grows
+        const StateView s = views[inst];
+        const int p = f - prefix[inst];
+        const int n = s.n;
+        const uint32_t t = (uint32_t)*s.t;
+        const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
         const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
         VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
         // V(t) -> shared memory with one bulk copy (tile padded to 16 bytes)
@@ -552,10 +561,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_velocity_sx(StateView s) {
 }
 
 template <int NW, typename VT>
-cudaError_t launch_vsx(const StateView& s, cudaStream_t st) {
-    int wpc = kWarps;  // warps (particles) per CTA, as many as shared memory allows
-    while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(s.n) > kSmemLimit) --wpc;
-    const size_t smem = kBarBytes + wpc * warp_bytes<VT>(s.n);
+cudaError_t launch_vsx(const VsxLaunch& L, cudaStream_t st) {
+    int wpc = L.warps > 0 ? L.warps : kWarps;  // warps (particles) per CTA
+    if (wpc > kWarps) wpc = kWarps;
+    while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(L.n_max) > kSmemLimit) --wpc;
+    const size_t smem = kBarBytes + wpc * warp_bytes<VT>(L.n_max);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -568,23 +578,24 @@ cudaError_t launch_vsx(const StateView& s, cudaStream_t st) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_velocity_sx<NW, VT>, wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
-    const int need = (s.P + wpc - 1) / wpc;
+    const int need = (L.total + wpc - 1) / wpc;
     if (grid > need) grid = need;
-    k_velocity_sx<NW, VT><<<grid, wpc * 32, smem, st>>>(s);
+    if (grid < 1) grid = 1;
+    k_velocity_sx<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t launch_vsx_t(const StateView& s, cudaStream_t st) {
-    switch ((s.n + 31) / 32) {
-        case 1: return launch_vsx<1, VT>(s, st);
-        case 2: return launch_vsx<2, VT>(s, st);
-        case 3: return launch_vsx<3, VT>(s, st);
-        case 4: return launch_vsx<4, VT>(s, st);
-        case 5: return launch_vsx<5, VT>(s, st);
+cudaError_t launch_vsx_t(const VsxLaunch& L, cudaStream_t st) {
+    switch ((L.n_max + 31) / 32) {
+        case 1: return launch_vsx<1, VT>(L, st);
+        case 2: return launch_vsx<2, VT>(L, st);
+        case 3: return launch_vsx<3, VT>(L, st);
+        case 4: return launch_vsx<4, VT>(L, st);
+        case 5: return launch_vsx<5, VT>(L, st);
         case 6:
         case 7:
-        case 8: return launch_vsx<8, VT>(s, st);
+        case 8: return launch_vsx<8, VT>(L, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -612,9 +623,10 @@ cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_velocity_sx(const StateView& s, int v_bf16, cudaStream_t st) {
-    if (s.n > velocity_sx_max_n(v_bf16)) return cudaErrorInvalidValue;
-    return v_bf16 ? launch_vsx_t<__nv_bfloat16>(s, st) : launch_vsx_t<float>(s, st);
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
+    if (L.total <= 0) return cudaSuccess;
+    if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
+    return L.v_bf16 ? launch_vsx_t<__nv_bfloat16>(L, st) : launch_vsx_t<float>(L, st);
 }
 
 }  // namespace qap

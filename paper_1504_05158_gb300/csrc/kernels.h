@@ -1,4 +1,8 @@
 // Host-side launchers of the PSO-iteration kernels (internal to the library).
+//
+// Every launcher covers a table of populations (one or many instances of possibly
+// different n) in a single kernel launch: the kernels read each population's view
+// or arguments from a small device table.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,8 +12,8 @@
 
 namespace qap {
 
-// Arguments of the goal-function / local-search kernel. Permutations are uint8
-// rows (facility -> location) `ps_in` / `ps_out` bytes apart.
+// Arguments of the goal-function / local-search kernels for one population.
+// Permutations are uint8 rows (facility -> location) `ps_in` / `ps_out` bytes apart.
 struct LsArgs {
     int32_t n, count;
     int32_t ps_in, ps_out;
@@ -26,18 +30,44 @@ struct LsArgs {
     int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
     int32_t tc_exact;  // symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
                        // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT)
-    int32_t* work;     // device counter handing out particles (zeroed per launch), may be null
+    int32_t* work;     // device counter handing out this population's particles (zeroed
+                       // by the launcher before every launch)
 };
 
-// Largest n the local search supports (one warp's G matrix in shared memory).
+// Which local-search kernel serves a population, and the launch shape.
+enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2 };
+LsKind ls_kind(const LsArgs& a);
+
+// One local-search launch over `count` populations of the same kind.
+struct LsLaunch {
+    const LsArgs* d_args;  // device table, `count` entries
+    int32_t* d_work;       // the populations' counters (contiguous, `count` ints)
+    int count;
+    int n_max;             // largest n in the table (shared-memory layout)
+    int kind;              // LsKind
+    int cpi;               // CTAs per population (0 = automatic)
+    int total;             // particles over the table (automatic shape)
+};
+cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st);
 int ls_max_n();
-cudaError_t launch_ls(const LsArgs& a, cudaStream_t st);
+
+// One velocity + S_x launch over `count` populations (flat index over particles).
+struct VsxLaunch {
+    const StateView* d_views;
+    const int32_t* d_prefix;  // count + 1 particle offsets
+    int count;
+    int n_max;
+    int total;                // prefix[count]
+    int v_bf16;               // every population of the table has the same storage
+    int warps;                // warps per CTA (0 = automatic)
+};
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st);
+int velocity_sx_max_n(int v_bf16);
 
 cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st);
-cudaError_t launch_velocity_sx(const StateView& s, int v_bf16, cudaStream_t st);
-int velocity_sx_max_n(int v_bf16);
-// init_mode: the bookkeeping after initialisation (no migration, t unchanged).
-cudaError_t launch_bests(const StateView& s, int init_mode, cudaStream_t st);
+// One CTA per population; init_mode: the bookkeeping after initialisation (no
+// migration, t unchanged).
+cudaError_t launch_bests(const StateView* d_views, int count, int m_max, int init_mode, cudaStream_t st);
 int bests_max_swarms();
 
 // Sorts `count` costs in `scratch` (>= next power of two entries) and writes

@@ -7,38 +7,11 @@
 #include <new>
 #include <vector>
 
-#include "../../include/qap_pso.h"
-#include "kernels.h"
+#include "state.h"
 
 using namespace qap;
 
-struct qap_instance {
-    int32_t n;
-    int32_t* dF;
-    int32_t* dD;
-    int32_t sym_zd;
-    int32_t max_f, max_d;
-    int32_t exact32;
-    int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
-    int32_t tc_exact;   // the tensor-core set-up of the local search is exact
-};
-
-struct pso_state {
-    qap_instance* inst;
-    pso_params_t prm;
-    uint64_t seed;
-    cudaStream_t stream;
-    bool own_stream;
-    StateView sv;
-    void* dbase;
-    int64_t* stats_buf;
-    int32_t stats_len;
-    int64_t* stats_out;  // 6 int64 + 1 double
-    int32_t* work;       // particle counter of the local-search kernel
-    cudaGraphExec_t g1, g16;
-};
-
-namespace {
+namespace qap {
 
 int status_of(cudaError_t e) {
     if (e == cudaSuccess) return QAP_OK;
@@ -85,7 +58,7 @@ int validate(const qap_instance* inst, const pso_params_t* p) {
     return QAP_OK;
 }
 
-LsArgs ls_args_for(const pso_state* s, bool init) {
+LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work) {
     LsArgs a{};
     a.n = s->sv.n;
     a.count = s->sv.P;
@@ -102,17 +75,30 @@ LsArgs ls_args_for(const pso_state* s, bool init) {
     a.counters = init ? nullptr : s->sv.counters;
     a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
     a.tc_exact = s->inst->tc_exact;
-    a.work = s->work;
+    a.work = work;
     return a;
 }
 
+// Random particles, costs, bests; iteration counter and counters back to zero.
+cudaError_t reinit_state(pso_state* s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(s->sv.counters, 0, CNT_N * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.t, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = launch_init(s->sv, s->prm.v_storage == PSO_V_BF16, st);
+    if (e == cudaSuccess) e = launch_ls(s->ls_init, st);
+    if (e == cudaSuccess) e = launch_bests(s->d_view, 1, s->sv.m, 1, st);
+    return e;
+}
+
+}  // namespace qap
+
+namespace {
+
 cudaError_t enqueue_iteration(pso_state* s) {
-    const int bf = s->prm.v_storage == PSO_V_BF16;
-    cudaError_t e = launch_velocity_sx(s->sv, bf, s->stream);
+    cudaError_t e = launch_velocity_sx(s->vsx, s->stream);
     if (e != cudaSuccess) return e;
-    e = launch_ls(ls_args_for(s, false), s->stream);
+    e = launch_ls(s->ls_iter, s->stream);
     if (e != cudaSuccess) return e;
-    return launch_bests(s->sv, 0, s->stream);
+    return launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
 }
 
 cudaError_t capture(pso_state* s, int iters, cudaGraphExec_t* out) {
@@ -273,7 +259,8 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     const size_t ocostG = take((size_t)m * 8), ocostG2 = take((size_t)m * 8);
     const size_t obest = take(sv.ps), obc = take(8), obi = take(4), ot = take(4);
     const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
-    const size_t owork = take(4);
+    const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
+    const size_t owork = take(2 * 4);
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -301,7 +288,10 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     sv.counters = (unsigned long long*)(base + ocnt);
     s->stats_buf = (int64_t*)(base + ostb);
     s->stats_out = (int64_t*)(base + osto);
-    s->work = (int32_t*)(base + owork);
+    s->d_view = (StateView*)(base + oview);
+    s->d_prefix = (int32_t*)(base + opre);
+    s->d_ls = (LsArgs*)(base + ols);
+    s->d_work = (int32_t*)(base + owork);
     sv.seed = seed;
     sv.c1 = params->c1;
     sv.c2 = params->c2;
@@ -318,10 +308,19 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     sv.mig_period = params->mig_period;
     sv.ring_if_better = params->ring_if_better;
 
+    // one-entry tables the kernels read this population through
+    s->h_ls[0] = ls_args_for(s, false, s->d_work);
+    s->h_ls[1] = ls_args_for(s, true, s->d_work + 1);
+    s->h_prefix[0] = 0;
+    s->h_prefix[1] = P;
+    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0};
+    s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
+    s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     e = cudaMemsetAsync(base, 0, off, s->stream);
-    if (e == cudaSuccess) e = launch_init(sv, params->v_storage == PSO_V_BF16, s->stream);
-    if (e == cudaSuccess) e = launch_ls(ls_args_for(s, true), s->stream);
-    if (e == cudaSuccess) e = launch_bests(sv, 1, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_view, &s->sv, sizeof(StateView), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_prefix, s->h_prefix, sizeof(s->h_prefix), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(s->h_ls), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = reinit_state(s, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         pso_destroy(s);
@@ -358,16 +357,15 @@ int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t fl
     cudaError_t e = cudaSuccess;
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
-    const int bf = s->prm.v_storage == PSO_V_BF16;
     for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
         cudaEvent_t* q = &ev[(size_t)i * 4];
         if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(q[0], s->stream);
-        if (e == cudaSuccess) e = launch_velocity_sx(s->sv, bf, s->stream);
+        if (e == cudaSuccess) e = launch_velocity_sx(s->vsx, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(q[1], s->stream);
-        if (e == cudaSuccess) e = launch_ls(ls_args_for(s, false), s->stream);
+        if (e == cudaSuccess) e = launch_ls(s->ls_iter, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(q[2], s->stream);
-        if (e == cudaSuccess) e = launch_bests(s->sv, 0, s->stream);
+        if (e == cudaSuccess) e = launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(q[3], s->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -618,7 +616,12 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
         a.max_moves = max_moves;
         a.tc_exact = inst->tc_exact;
         a.work = dw;
-        e = launch_ls(a, 0);
+        LsArgs* da = nullptr;
+        e = cudaMalloc(&da, sizeof(LsArgs));
+        if (e == cudaSuccess) e = cudaMemcpy(da, &a, sizeof(LsArgs), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_ls(LsLaunch{da, dw, 1, n, (int)ls_kind(a), 0, count}, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(da);
     }
     std::vector<int64_t> hc(count);
     std::vector<int32_t> hm(count), hr(count);

@@ -1,0 +1,49 @@
+// Internal definitions of the C-ABI handles, shared by the runtime and the batch
+// engine (not part of the public header).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/qap_pso.h"
+#include "kernels.h"
+
+struct qap_instance {
+    int32_t n;
+    int32_t* dF;
+    int32_t* dD;
+    int32_t sym_zd;
+    int32_t max_f, max_d;
+    int32_t exact32;
+    int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
+    int32_t tc_exact;   // the tensor-core set-up of the local search is exact
+};
+
+// One population. Its kernels read it through one-entry device tables (the same
+// kernels serve a batch of many populations with longer tables).
+struct pso_state {
+    qap_instance* inst;
+    pso_params_t prm;
+    uint64_t seed;
+    cudaStream_t stream;
+    bool own_stream;
+    qap::StateView sv;
+    void* dbase;
+    int64_t* stats_buf;
+    int32_t stats_len;
+    int64_t* stats_out;       // 6 int64 + 1 double
+    qap::StateView* d_view;   // 1 entry
+    int32_t* d_prefix;        // {0, P}
+    qap::LsArgs* d_ls;        // [0] iteration, [1] initialisation
+    int32_t* d_work;          // their particle counters
+    qap::LsArgs h_ls[2];      // host copies (sources of the uploads)
+    int32_t h_prefix[2];
+    qap::VsxLaunch vsx;
+    qap::LsLaunch ls_iter, ls_init;
+    cudaGraphExec_t g1, g16;
+};
+
+namespace qap {
+int status_of(cudaError_t e);
+LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work);
+cudaError_t reinit_state(pso_state* s, cudaStream_t st);
+}  // namespace qap

@@ -26,7 +26,8 @@ EXPORTS = [
     "qap_status_string", "qap_create_instance", "qap_destroy_instance", "qap_instance_info",
     "pso_params_default", "pso_init", "pso_step", "pso_step_timed", "pso_best", "pso_stats", "pso_destroy",
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
-    "qap_cost_stats_noalloc",
+    "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
+    "pso_batch_size", "pso_batch_member", "pso_batch_destroy",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -112,6 +113,13 @@ def lib():
         L.qap_eval_costs.argtypes = [vp, vp, C.c_int32, vp]
         L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.qap_cost_stats_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double)]
+        L.pso_batch_create.argtypes = [C.c_int32, vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
+        L.pso_batch_step.argtypes = [vp, C.c_int32]
+        L.pso_batch_step_timed.argtypes = [vp, C.c_int32, vp, C.c_size_t, C.POINTER(C.c_float)]
+        L.pso_batch_size.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.pso_batch_member.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+        L.pso_batch_destroy.argtypes = [vp]
+        L.pso_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -204,11 +212,15 @@ class Instance:
 class Swarm:
     """Population state of one PSO run on the device."""
 
-    def __init__(self, inst: Instance, params: Params, seed: int, stream=None):
+    def __init__(self, inst: Instance, params: Params, seed: int, stream=None, _handle=None):
         self.inst = inst  # keeps the instance alive
         self.params = params
         self.n = inst.n
         self.P = params.swarms * params.swarm_size
+        self._owned = _handle is None
+        if _handle is not None:
+            self.h = _handle
+            return
         h = C.c_void_p()
         st = C.c_void_p(stream) if stream else None
         _check(lib().pso_init(inst.h, C.byref(params), seed, st, C.byref(h)), "pso_init")
@@ -268,7 +280,54 @@ class Swarm:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().pso_destroy(self.h)
+            if self._owned:
+                lib().pso_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many populations (instances of uneven n) advanced by shared launches."""
+
+    def __init__(self, instances, params, seeds, stream=None, autotune=True):
+        self.instances = list(instances)
+        self.params = list(params)
+        k = len(self.instances)
+        if len(self.params) != k or len(seeds) != k:
+            raise ValueError("instances, params and seeds must have equal length")
+        handles = (C.c_void_p * k)(*[i.h for i in self.instances])
+        parr = (Params * k)(*self.params)
+        sarr = (C.c_uint64 * k)(*[int(s) for s in seeds])
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        _check(lib().pso_batch_create(k, handles, parr, sarr, st, 1 if autotune else 0, C.byref(h)),
+               "pso_batch_create")
+        self.h = h
+        self.members = []
+        for i in range(k):
+            mh = C.c_void_p()
+            _check(lib().pso_batch_member(self.h, i, C.byref(mh)), "pso_batch_member")
+            self.members.append(Swarm(self.instances[i], self.params[i], 0, _handle=mh))
+
+    def step(self, iterations=1):
+        _check(lib().pso_batch_step(self.h, iterations), "pso_batch_step")
+
+    def step_timed(self, iterations=1, flush_ptr=None, flush_bytes=0):
+        ms = (C.c_float * 4)()
+        fp = C.c_void_p(flush_ptr) if flush_ptr else None
+        _check(lib().pso_batch_step_timed(self.h, iterations, fp, flush_bytes, ms), "pso_batch_step_timed")
+        return [ms[0], ms[1], ms[2], ms[3]]
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            lib().pso_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -319,6 +319,75 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------- other workloads
+
+def run_batch(args):
+    """64 instances with n uniform in [20, 128] (half dense uniform, half grid with
+    sparse flows), 8 swarms x 256 particles each, bf16 velocity storage, all in one
+    batch (one launch per phase, graph replay, autotuned shapes)."""
+    import torch
+
+    from paper_1504_05158_gb300 import build as B
+    B.build()
+    from paper_1504_05158_gb300 import qap_pso as Q
+    from paper_1504_05158_gb300 import workloads as W
+    insts = W.uneven_batch(64)
+    gis = [Q.Instance(i.F, i.D) for i in insts]
+    prm = [Q.default_params(swarms=8, swarm_size=256, v_storage=Q.V_BF16) for _ in insts]
+    b = Q.Batch(gis, prm, [4096 + i for i in range(len(insts))], autotune=True)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = b.step_timed(args.steps, flush.data_ptr(), flush.numel())
+    P = sum(p.swarms * p.swarm_size for p in prm)
+    ns = [i.n for i in insts]
+    out = {"metric": "particle-iterations/s, uneven batch", "value": P * args.steps / (ms[3] / 1e3),
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms[3] / args.steps, "higher_is_better": True, "dtype": "f32 (bf16 V)",
+           "data": "synthetic",
+           "config": {"workload": "64 instances, n uniform in [20, 128], 8 x 256 particles each, bf16 V",
+                      "n_min": min(ns), "n_max": max(ns), "particles": P,
+                      "ls_kernels": {"team1 (n<=32)": sum(n <= 32 for n in ns),
+                                     "team2 (n<=64)": sum(32 < n <= 64 for n in ns),
+                                     "team8 (n<=128)": sum(64 < n <= 128 for n in ns),
+                                     "simt (n>128)": sum(n > 128 for n in ns)}},
+           "kernel_ms_per_step": {"velocity_sx": ms[0] / args.steps, "cost_ls": ms[1] / args.steps,
+                                  "bests_migration": ms[2] / args.steps},
+           "clocks": clk.summary(), "gpu_launches": None}
+    print(json.dumps(out))
+    b.close()
+
+
+def run_serve(args):
+    """Poisson arrivals at args.rate requests/s for args.duration s; each request a
+    fresh instance with n in {32, 64, 100, 150}, 4 096-16 384 particles in 8-32
+    swarms, 150 iterations; admitted under a 120 GB device-memory budget."""
+    import torch
+
+    from paper_1504_05158_gb300 import build as B
+    B.build()
+    from paper_1504_05158_gb300 import serve as S
+    from paper_1504_05158_gb300 import workloads as W
+    reqs = W.serving_stream(rate_hz=args.rate, duration_s=args.duration, iterations=args.serve_iters)
+    jobs = S.jobs_from_stream(reqs)
+    torch.cuda.synchronize()
+    srv = S.Server(budget_bytes=120 * 10**9, inflight_particles=args.inflight)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        rep = srv.run(jobs, realtime=True)
+    summ = rep.summary()
+    out = {"metric": "serving: latency p50/p99 and aggregate particle-iterations/s", "unit": UNIT,
+           "value": summ["particle_iterations_per_s"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+           "requests": summ["requests"], "makespan_s": summ["makespan_s"],
+           "peak_bytes": summ["peak_bytes"], "peak_slots": summ["peak_slots"],
+           "peak_inflight_particles": summ["peak_inflight_particles"],
+           "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, n in {{32,64,100,150}}, "
+                                  f"4096-16384 particles, {args.serve_iters} iterations, 120 GB budget",
+                      "inflight_particles": args.inflight},
+           "higher_is_better": True, "data": "synthetic", "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,6 +398,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="fp32,bf16",
                     help="velocity storage formats to time (fp32 is the headline)")
+    ap.add_argument("--workload", choices=("grid64", "batch64", "serve"), default="grid64",
+                    help="grid64: the headline n = 64 workload; batch64 / serve: the batch and "
+                         "serving workloads (separate JSON lines)")
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--serve-iters", type=int, default=150)
+    ap.add_argument("--inflight", type=int, default=49152,
+                    help="serving: particles with work in flight at once (oldest requests first)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -337,6 +414,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch64":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args, rank, world, local_rank)
 

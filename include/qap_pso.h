@@ -134,6 +134,14 @@ int pso_step(pso_state_t st, int32_t iterations);
 int pso_step_timed(pso_state_t st, int32_t iterations, void* flush_buf, size_t flush_bytes,
                    float* ms_out);
 
+/* Device bytes pso_init would allocate for a population of this instance size and
+ * these parameters (for admission against a memory budget). */
+int pso_footprint(int32_t n, const pso_params_t* params, size_t* bytes);
+
+/* *done = 1 when every operation queued on the state's stream has finished, else
+ * 0 (never waits). */
+int pso_poll(pso_state_t st, int32_t* done);
+
 /* Best solution found so far (synchronises): its cost, its permutation (n
  * entries, may be NULL) and the number of completed iterations when it was found
  * (0 = during initialisation). */
@@ -189,7 +197,7 @@ int pso_import_state(pso_state_t st, const pso_host_state_t* in);
 /* Many independent populations advanced together, e.g. many QAP instances of
  * different n (the multi-swarm method of section 3 applied to each). Every phase
  * of an iteration runs as one kernel launch over all members (the local search
- * as one launch per kernel kind present: tensor-core set-up for n <= 64 with small
+ * as one launch per kernel kind present: tensor-core set-up for n <= 128 with small
  * entries, SIMT set-up otherwise); iterations are replayed from a captured CUDA
  * graph. Results of every member are identical to running it alone. */
 typedef struct pso_batch* pso_batch_t;

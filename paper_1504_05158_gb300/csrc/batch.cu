@@ -183,10 +183,10 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
         m_max = std::max(m_max, (int)s->sv.m);
     }
     b->m_max = m_max;
-    int kind_count[3] = {0, 0, 0};
+    int kind_count[LS_KINDS] = {0, 0, 0, 0};
     for (auto* s : b->members) ++kind_count[s->ls_iter.kind];
     size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024;
-    for (int k = 0; k < 3; ++k) bytes += (sizeof(LsArgs) + sizeof(int32_t)) * kind_count[k] + 512;
+    for (int k = 0; k < LS_KINDS; ++k) bytes += (sizeof(LsArgs) + sizeof(int32_t)) * kind_count[k] + 512;
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, bytes);
     if (e != cudaSuccess) {
@@ -205,7 +205,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     e = cudaMemcpy(b->d_views, b->h_views.data(), sizeof(StateView) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_prefix, b->h_prefix.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < LS_KINDS && e == cudaSuccess; ++k) {
         if (!kind_count[k]) continue;
         Group g;
         LsArgs* d_args = (LsArgs*)take(sizeof(LsArgs) * kind_count[k]);
@@ -281,7 +281,7 @@ int pso_batch_step_timed(pso_batch_t b, int32_t iterations, void* flush_buf, siz
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {  // velocity, search, bests
             float ms = 0.f;
             e = cudaEventElapsedTime(&ms, ev[(size_t)i * 4 + k], ev[(size_t)i * 4 + k + 1]);
             acc[k] += ms;

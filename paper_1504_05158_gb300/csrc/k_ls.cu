@@ -15,7 +15,7 @@
 // so a round costs O(1) per pair after an O(n^3) set-up per iteration.
 //
 // The set-up G = F * D_p is a dense product. Two kernels form it:
-//   k_ls_team (n <= 64, symmetric, entries <= 2048, n max_f max_d < 2^24): on the
+//   k_ls_team (n <= 128, symmetric, entries <= 2048, n max_f max_d < 2^24): on the
 //     tensor cores (tcgen05, fp16 operands, fp32 accumulation in tensor memory).
 //     Every operand and partial sum is an integer below 2^24, so the fp32 result is
 //     exact. With G[k][l] = sum_j' F[k][p^-1(j')] D[j'][l], the A operand is F with
@@ -301,17 +301,20 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
 }
 
 // ------------------------------------------------------ tensor-core set-up
-// Teams of WPP warps (WPP = 1 for n <= 32, 2 for n <= 64) search one particle at a
-// time, independently of the other teams of the CTA. A team's particle occupies the
-// rows of an M = 128 A tile that sit in the tensor-memory lane quarters of the
-// team's own warps (the other rows are never read back), the team has its own
-// tensor-memory columns and mbarrier, and particles come from a global counter, so
-// no team waits for another team's search. KP = NP = n rounded up to 16.
+// Teams of WPP warps (1 for n <= 32, 2 for n <= 64, 8 for n <= 128) search one
+// particle at a time, independently of the other teams of the CTA. A team's
+// particle occupies the rows of an M = 128 A tile that sit in the tensor-memory
+// lane quarters of the team's own warps (rows of other quarters are never read
+// back), the team has its own tensor-memory columns and mbarrier, and particles come
+// from a per-population counter, so no team waits for another team's search.
+// KP = NP = n rounded up to 16. The search reads F from its fp16 copy (exact).
 template <int WPP>
 struct TeamLayout {
     int n, KP, NP, fhs;
-    size_t oF, oD, oFh, oB, oPin, oGd, oPi, oX, oBar, oT, oU, ubytes, total;
+    size_t oD, oFh, oB, oPin, oGd, oPi, oX, oBar, oT, oU, ubytes, total;
 };
+
+constexpr int kXchBytes = 256;  // per team: reduction slots and the next particle
 
 template <int WPP>
 __host__ __device__ inline TeamLayout<WPP> team_layout(int n) {
@@ -327,14 +330,13 @@ __host__ __device__ inline TeamLayout<WPP> team_layout(int n) {
         o = (o + b + 127) & ~size_t(127);
         return r;
     };
-    L.oF = take((size_t)n * round_up(n, 4) * 4);
     L.oD = take((size_t)n * n * 2);
     L.oFh = take((size_t)n * L.fhs * 2);
     L.oB = take((size_t)L.NP * L.KP * 2);
-    L.oPin = take(TEAMS * 64);
+    L.oPin = take(TEAMS * 128);
     L.oGd = take(TEAMS * align16((size_t)n * 4));
     L.oPi = take(TEAMS * align16((size_t)n * 4));
-    L.oX = take(TEAMS * 64);  // per team: next particle, reduction slots
+    L.oX = take(TEAMS * kXchBytes);
     L.oBar = take(TEAMS * 8);
     L.oT = take(16);
     const size_t a_bytes = (size_t)128 * L.KP * 2;
@@ -366,7 +368,7 @@ __device__ __forceinline__ bool team_all(bool v, int team) {
     return r != 0;
 }
 
-// team-wide lexicographic minimum of (value, key); xch: 2 x WPP x 2 ints, used
+// team-wide lexicographic minimum of (value, key); xch ints [0, 4 WPP) used
 // alternately (`parity`) so consecutive reductions need a single barrier each
 template <int WPP>
 __device__ __forceinline__ void team_min2(int& v, unsigned& key, int* xch, int parity, int team, int lane,
@@ -412,15 +414,24 @@ __device__ __forceinline__ long long team_sum64(long long v, long long* xch, int
     return t;
 }
 
-// Best-improvement descent of particle p by one team from a complete G: thread tt
-// owns pair slot e = tt of every virtual row and column l = tt of G.
+__device__ __forceinline__ int fval(const __half* sFh, int fhs, int k, int m) {
+    return __half2int_rn(sFh[k * fhs + m]);
+}
+
+// Best-improvement descent of particle p by one team from a complete G. The team's
+// threads form `nph` phases of `slotw` threads: thread (ph, e) evaluates pair slot e
+// of virtual rows ph, ph + nph, ... and, after a move, updates column e of G in rows
+// ph, ph + nph, ...
 template <int WPP>
-__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32_t* sF, const uint16_t* sD,
-                                             int32_t* G, int32_t* gd, int32_t* pi, int* xch, int tt,
-                                             int team) {
+__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const __half* sFh, int fhs,
+                                             const uint16_t* sD, int32_t* G, int32_t* gd, int32_t* pi,
+                                             int* xch, int tt, int team) {
     constexpr int TT = 32 * WPP;
-    const int n = a.n, fs = round_up(n, 4), gs = n + 1;
+    const int n = a.n, gs = n + 1;
     const int lane = tt & 31, wi = tt >> 5;
+    const int slotw = round_up(n, 32) < TT ? round_up(n, 32) : TT;
+    const int nph = TT / slotw, ph = tt / slotw, e = tt % slotw;
+    const bool on = ph < nph && e < n;
     const long long npairs = (long long)n * (n - 1) / 2;
     const int nv = n / 2;
     long long part = 0;
@@ -428,7 +439,7 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32
         gd[m] = G[m * gs + pi[m]];
         part += gd[m];
     }
-    long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch + 8), team, lane, wi);
+    long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, wi);
     int moves = 0, rounds = 0;
     if (a.max_moves >= 0) {
         for (;;) {
@@ -439,9 +450,8 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32
             }
             int best = INT_MAX;
             unsigned bkey = 0xFFFFFFFFu;
-            const int e = tt;
-            if (e < n) {
-                for (int t = 0; t < nv; ++t) {
+            if (on) {
+                for (int t = ph; t < nv; t += nph) {
                     int k, m;
                     if (e < n - 1 - t) {
                         k = t;
@@ -453,7 +463,7 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32
                     }
                     const int pk = pi[k], pmm = pi[m];
                     const int d = 2 * (G[k * gs + pmm] + G[m * gs + pk] - gd[k] - gd[m]) +
-                                  4 * sF[k * fs + m] * (int)sD[pk * n + pmm];
+                                  4 * fval(sFh, fhs, k, m) * (int)sD[pk * n + pmm];
                     const unsigned key = ((unsigned)k << 8) | (unsigned)m;
                     if (d < best || (d == best && key < bkey)) {
                         best = d;
@@ -470,9 +480,10 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const int32
                 break;
             }
             const int pr = pi[r], pss = pi[s];
-            if (tt < n) {
-                const int bt = (int)sD[pss * n + tt] - (int)sD[pr * n + tt];
-                for (int k = 0; k < n; ++k) G[k * gs + tt] += (sF[r * fs + k] - sF[s * fs + k]) * bt;
+            if (on) {
+                const int bt = (int)sD[pss * n + e] - (int)sD[pr * n + e];
+                for (int k = ph; k < n; k += nph)
+                    G[k * gs + e] += (fval(sFh, fhs, r, k) - fval(sFh, fhs, s, k)) * bt;
             }
             team_sync<WPP>(team);  // G complete; p itself is still the old one
             for (int m = tt; m < n; m += TT) {
@@ -518,24 +529,23 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
     constexpr int TT = 32 * WPP, TEAMS = 8 / WPP;
     const LsArgs a = args[blockIdx.x / cpi];
     const int cb = blockIdx.x % cpi;
-    const int n = a.n, fs = round_up(n, 4);
+    const int n = a.n;
     const TeamLayout<WPP> L = team_layout<WPP>(n);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int team = warp / WPP, tt = tid - team * TT;
-    int32_t* sF = reinterpret_cast<int32_t*>(smem + L.oF);
     uint16_t* sD = reinterpret_cast<uint16_t*>(smem + L.oD);
     __half* sFh = reinterpret_cast<__half*>(smem + L.oFh);
     unsigned char* sB = smem + L.oB;
-    uint8_t* pinv = smem + L.oPin + team * 64;
+    uint8_t* pinv = smem + L.oPin + team * 128;
     int32_t* gd = reinterpret_cast<int32_t*>(smem + L.oGd + team * align16((size_t)n * 4));
     int32_t* pi = reinterpret_cast<int32_t*>(smem + L.oPi + team * align16((size_t)n * 4));
-    int* xch = reinterpret_cast<int*>(smem + L.oX + team * 64);
+    int* xch = reinterpret_cast<int*>(smem + L.oX + team * kXchBytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.oBar) + team;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.oT);
     unsigned char* U = smem + L.oU + (size_t)team * L.ubytes;
     int32_t* G = reinterpret_cast<int32_t*>(U);
 
-    stage_fd(a, sF, sD, fs);
+    for (int i = tid; i < n * n; i += blockDim.x) sD[i] = (uint16_t)a.D[i];
     for (int i = tid; i < n * L.fhs; i += blockDim.x) {
         const int r = i / L.fhs, c = i % L.fhs;
         sFh[i] = __int2half_rn(c < n ? a.F[r * n + c] : 0);
@@ -559,6 +569,7 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
     const uint32_t sbo = (uint32_t)(L.KP / 8) * 128;
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
     const int wq = warp & 3;                      // this warp's lane quarter
+    const bool reader = (warp % WPP) < 4;         // warps that read the team's rows back
     uint32_t phase = 0;
     int next = cb * TEAMS + team;
     const int stride = cpi * TEAMS;
@@ -566,9 +577,9 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
     for (;;) {
         int p;
         if (a.work) {
-            if (tt == 0) xch[15] = atomicAdd(a.work, 1);
+            if (tt == 0) xch[60] = atomicAdd(a.work, 1);
             team_sync<WPP>(team);
-            p = xch[15];
+            p = xch[60];
             team_sync<WPP>(team);
         } else {
             p = next;
@@ -586,9 +597,9 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
             for (int c = 0; c < L.KP; c += 8) {
                 __align__(16) __half h[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = c + e;
-                    h[e] = j < n ? sFh[k * L.fhs + pinv[j]] : __int2half_rn(0);
+                for (int q = 0; q < 8; ++q) {
+                    const int j = c + q;
+                    h[q] = j < n ? sFh[k * L.fhs + pinv[j]] : __int2half_rn(0);
                 }
                 *reinterpret_cast<uint4*>(U + tc::tile_offset(rowbase + k, c, L.KP)) =
                     *reinterpret_cast<uint4*>(h);
@@ -611,8 +622,8 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
             break;
         }
         tc::fence_after_sync();
-        // G from tensor memory: this warp's quarter holds rows k = 32 (warp % WPP) + lane
-        {
+        // G from tensor memory: reader warp w holds rows k = 32 (w % WPP) + lane of its quarter
+        if (reader) {
             const int k = 32 * (warp % WPP) + lane;
             for (int c = 0; c < L.NP; c += 16) {
                 uint32_t v[16];
@@ -621,14 +632,14 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
                 // G overwrites the A tile, which the completed product no longer reads
                 if (k < n) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        if (c + e < n) G[k * (n + 1) + c + e] = __float2int_rn(__uint_as_float(v[e]));
+                    for (int q = 0; q < 16; ++q)
+                        if (c + q < n) G[k * (n + 1) + c + q] = __float2int_rn(__uint_as_float(v[q]));
                 }
             }
         }
         tc::fence_before_sync();
         team_sync<WPP>(team);
-        descend_team<WPP>(a, p, sF, sD, G, gd, pi, xch, tt, team);
+        descend_team<WPP>(a, p, sFh, L.fhs, sD, G, gd, pi, xch, tt, team);
         team_sync<WPP>(team);
     }
     tc::fence_before_sync();
@@ -715,8 +726,8 @@ int ls_max_n() {
 LsKind ls_kind(const LsArgs& a) {
     const char* env = getenv("QAP_PSO_LS_SETUP");
     const bool simt = env && strcmp(env, "simt") == 0;
-    if (!a.tc_exact || a.n > 64 || simt) return LS_SIMT;
-    return a.n <= 32 ? LS_TEAM1 : LS_TEAM2;
+    if (!a.tc_exact || a.n > 128 || simt) return LS_SIMT;
+    return a.n <= 32 ? LS_TEAM1 : (a.n <= 64 ? LS_TEAM2 : LS_TEAM8);
 }
 
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
@@ -724,6 +735,7 @@ cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
     if (L.n_max < 2 || L.n_max > ls_max_n()) return cudaErrorInvalidValue;
     if (L.kind == LS_TEAM1) return launch_team<1>(L, st);
     if (L.kind == LS_TEAM2) return launch_team<2>(L, st);
+    if (L.kind == LS_TEAM8) return launch_team<8>(L, st);
     switch ((L.n_max + 31) / 32) {
         case 1: return launch_nw<1>(L, st);
         case 2: return launch_nw<2>(L, st);

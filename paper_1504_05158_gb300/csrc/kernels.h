@@ -35,7 +35,7 @@ struct LsArgs {
 };
 
 // Which local-search kernel serves a population, and the launch shape.
-enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2 };
+enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_KINDS = 4 };
 LsKind ls_kind(const LsArgs& a);
 
 // One local-search launch over `count` populations of the same kind.

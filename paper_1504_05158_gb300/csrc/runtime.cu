@@ -330,6 +330,36 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     return QAP_OK;
 }
 
+int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
+    if (!p || !bytes || n < 2 || n > 256 || p->swarms < 1 || p->swarm_size < 1) return QAP_ERR_INVALID_ARG;
+    const size_t P = (size_t)p->swarms * p->swarm_size, m = (size_t)p->swarms;
+    const size_t ps = align_up(n, 16), vstride = align_up((size_t)n * n, 8);
+    const size_t esz = p->v_storage == PSO_V_BF16 ? 2 : 4;
+    size_t sl = 1;
+    while (sl < P) sl <<= 1;
+    const size_t a = 256;
+    size_t t = align_up(P * vstride * esz, a) + 3 * align_up(P * ps, a) + 2 * align_up(P * 8, a) +
+               2 * align_up(P * 4, a) + 2 * align_up(m * ps, a) + 2 * align_up(m * 8, a) + 4 * a +
+               align_up(CNT_N * 8, a) + align_up(sl * 8, a) + align_up(7 * 8, a) +
+               align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a;
+    *bytes = t;
+    return QAP_OK;
+}
+
+int pso_poll(pso_state_t s, int32_t* done) {
+    if (!s || !done) return QAP_ERR_INVALID_ARG;
+    const cudaError_t e = cudaStreamQuery(s->stream);
+    if (e == cudaSuccess) {
+        *done = 1;
+        return QAP_OK;
+    }
+    if (e == cudaErrorNotReady) {
+        *done = 0;
+        return QAP_OK;
+    }
+    return status_of(e);
+}
+
 int pso_step(pso_state_t s, int32_t iterations) {
     if (!s || iterations < 0) return QAP_ERR_INVALID_ARG;
     if (iterations == 0) return QAP_OK;

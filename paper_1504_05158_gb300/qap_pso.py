@@ -27,7 +27,7 @@ EXPORTS = [
     "pso_params_default", "pso_init", "pso_step", "pso_step_timed", "pso_best", "pso_stats", "pso_destroy",
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
     "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
-    "pso_batch_size", "pso_batch_member", "pso_batch_destroy",
+    "pso_batch_size", "pso_batch_member", "pso_batch_destroy", "pso_footprint", "pso_poll",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -120,6 +120,8 @@ def lib():
         L.pso_batch_member.argtypes = [vp, C.c_int32, C.POINTER(vp)]
         L.pso_batch_destroy.argtypes = [vp]
         L.pso_batch_destroy.restype = None
+        L.pso_footprint.argtypes = [C.c_int32, C.POINTER(Params), C.POINTER(C.c_size_t)]
+        L.pso_poll.argtypes = [vp, C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -161,6 +163,13 @@ def cost_stats_noalloc(costs_dev_ptr, count, stream=None):
                                         C.byref(mean)), "qap_cost_stats_noalloc")
     return dict(min=int(out[0]), p5=int(out[1]), p25=int(out[2]), p50=int(out[3]),
                 p75=int(out[4]), max=int(out[5]), mean=mean.value)
+
+
+def footprint(n, params):
+    """Device bytes a population of size n with these parameters allocates."""
+    b = C.c_size_t()
+    _check(lib().pso_footprint(n, C.byref(params), C.byref(b)), "pso_footprint")
+    return b.value
 
 
 class Instance:
@@ -236,6 +245,12 @@ class Swarm:
         fp = C.c_void_p(flush_ptr) if flush_ptr else None
         _check(lib().pso_step_timed(self.h, iterations, fp, flush_bytes, ms), "pso_step_timed")
         return [ms[0], ms[1], ms[2], ms[3]]
+
+    def done(self):
+        """True when all work queued on this population's stream has finished."""
+        d = C.c_int32()
+        _check(lib().pso_poll(self.h, C.byref(d)), "pso_poll")
+        return bool(d.value)
 
     def best(self):
         c = C.c_int64()

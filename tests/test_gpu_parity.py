@@ -24,6 +24,7 @@ INSTANCES = {
     "n33": lambda: W.dense_uniform(33, 5),
     "grid64": W.grid64,
     "n65grid": lambda: W.grid_sparse(65, 6),
+    "n97": lambda: W.dense_uniform(97, 10),
     "n100": lambda: W.dense_uniform(100, 7),
     "n128grid": lambda: W.grid_sparse(128, 8),
     "n150": lambda: W.dense_uniform(150, 9),
@@ -236,7 +237,7 @@ def test_invalid_params(Q):
 
 
 @pytest.mark.parametrize("setup", ["tc", "simt"])
-@pytest.mark.parametrize("name", ["n3", "tiny9", "dense30", "n33", "grid64"])
+@pytest.mark.parametrize("name", ["n3", "tiny9", "dense30", "n33", "grid64", "n65grid", "n97", "n128grid"])
 def test_local_search_both_setups(Q, setup, name, monkeypatch):
     # the tensor-core and SIMT set-ups of G give identical searches
     if setup == "simt":

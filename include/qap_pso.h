@@ -233,6 +233,31 @@ int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds);
 
+/* Swap values of one permutation: out[idx(r, s)] = f(p o (r s)) - f(p) for every
+ * pair r < s, in r-major order (idx = r n - r (r + 1) / 2 + s - r - 1), by the
+ * general O(n) formula (any instance; int64 arithmetic). perm: host, n int32 (a
+ * permutation, facility -> location); out: host, n (n - 1) / 2 int64. Synchronous.
+ * Errors: QAP_ERR_INVALID_ARG (NULL pointer, not a permutation), QAP_ERR_OOM,
+ * QAP_ERR_CUDA. */
+int qap_delta_table(qap_instance_t inst, const int32_t* perm, int64_t* out);
+
+/* Position discretisation alone (S_x = SecondTarget, Algorithm 1 of section 3.1)
+ * of `count` matrices: Y (host, count x n x n fp32, row = location, column =
+ * facility) and Z (host, count x n int32 permutations, facility -> location; the
+ * ones of X(t)). The depth, sx_rule and tie_rule of `params` apply (its other
+ * fields are ignored); random ties draw from the same Philox stream as an
+ * iteration of particle particle[i] of swarm swarm[i] at iteration t (host arrays
+ * of count int32). out_perm: host, count x n int32. This is the S_x of pso_step
+ * with Y = X(t) + V formed by the caller, so the kernel compares exactly the given
+ * fp32 values. 2 <= n <= the device limit of the fp32 velocity kernel.
+ * Synchronous. Errors: QAP_ERR_INVALID_ARG (bad sizes, parameters, negative swarm
+ * or particle indices, Z not a permutation, non-finite Y), QAP_ERR_UNSUPPORTED
+ * (n too large), QAP_ERR_OOM, QAP_ERR_CUDA, QAP_ERR_TIMEOUT (a bounded wait gave
+ * up). */
+int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, const pso_params_t* params,
+                   uint64_t seed, const int32_t* swarm, const int32_t* particle, int32_t t,
+                   int32_t* out_perm);
+
 /* ------------------------------------------------ allocation-free statistics */
 /* The same statistics as pso_stats (min, 5/25/50/75 % nearest-rank percentiles,
  * max, mean), computed from `count` costs that the caller already holds in device

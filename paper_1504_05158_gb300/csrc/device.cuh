@@ -150,6 +150,11 @@ struct StateView {
     float c1, c2, c3, v_max;
     int32_t sv_kind, sx_rule, depth, tie_rule, pos_uses_new_v;
     int32_t ls_max_moves, mig_kind, mig_depth, mig_period, ring_if_better;
+    // S_x alone (the discretisation entry point): V holds Y itself, X holds Z, and
+    // the Philox counters of particle p are (sx_pis[p], sx_swarm[p], *t)
+    int32_t sx_only;
+    const int32_t* sx_swarm;
+    const int32_t* sx_pis;
 };
 
 // counters[CNT_ERR] counts internal consistency failures (a kernel that detects one

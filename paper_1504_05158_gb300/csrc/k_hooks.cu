@@ -1,0 +1,42 @@
+// The swap-value table of one permutation, for checking and inspection.
+//
+// Delta(r, s) = f(p o (r s)) - f(p) for every pair r < s, by the general O(n)
+// formula for a swap (any F and D; section 2.1's goal function):
+//   (F_rr - F_ss)(D_{p_s p_s} - D_{p_r p_r}) + (F_rs - F_sr)(D_{p_s p_r} - D_{p_r p_s})
+//   + sum_{k != r, s} (F_kr - F_ks)(D_{p_k p_s} - D_{p_k p_r})
+//                   + (F_rk - F_sk)(D_{p_s p_k} - D_{p_r p_k}),
+// accumulated in int64. One thread per pair; F and D are read through the cache.
+#include "kernels.h"
+
+namespace qap {
+namespace {
+
+__global__ void k_delta_table(const int32_t* __restrict__ F, const int32_t* __restrict__ D, int n,
+                              const int32_t* __restrict__ perm, int64_t* __restrict__ out) {
+    const int r = blockIdx.x;
+    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    if (s <= r || s >= n) return;
+    const int pr = perm[r], pss = perm[s];
+    long long d = (long long)(F[r * n + r] - F[s * n + s]) * (D[pss * n + pss] - D[pr * n + pr]) +
+                  (long long)(F[r * n + s] - F[s * n + r]) * (D[pss * n + pr] - D[pr * n + pss]);
+    for (int k = 0; k < n; ++k) {
+        if (k == r || k == s) continue;
+        const int pk = perm[k];
+        d += (long long)(F[k * n + r] - F[k * n + s]) * (D[pk * n + pss] - D[pk * n + pr]) +
+             (long long)(F[r * n + k] - F[s * n + k]) * (D[pss * n + pk] - D[pr * n + pk]);
+    }
+    const long long idx = (long long)r * n - (long long)r * (r + 1) / 2 + (s - r - 1);  // r-major
+    out[idx] = d;
+}
+
+}  // namespace
+
+cudaError_t launch_delta_table(const int32_t* F, const int32_t* D, int n, const int32_t* perm, int64_t* out,
+                               cudaStream_t st) {
+    if (n < 2) return cudaSuccess;
+    const dim3 grid((unsigned)n, (unsigned)((n + 127) / 128));
+    k_delta_table<<<grid, 128, 0, st>>>(F, D, n, perm, out);
+    return cudaGetLastError();
+}
+
+}  // namespace qap

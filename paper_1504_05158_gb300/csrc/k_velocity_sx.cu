@@ -158,9 +158,11 @@ __device__ __noinline__ int kth_row(const VT* tile, const uint32_t* dead, int n,
     return -1;
 }
 
-// SecondTarget (Algorithm 1) on Y = X(t) + tile for one particle; returns the
-// number of steps whose set M had more than one element and leaves the location
-// chosen for each owned column (facility) in newp.
+// SecondTarget (Algorithm 1) on Y for one particle; returns the number of steps
+// whose set M had more than one element and leaves the location chosen for each
+// owned column (facility) in newp. The tile holds V with Y = X(t) + V (zadd = 1:
+// the X(t) cell of column c is tile[pz][c] + 1, every other cell the tile value),
+// or Y itself (zadd = 0).
 //
 // After the first `depth` steps, every X(t) cell that exceeds all remaining plain
 // values (bound P0) is taken by the greedy in descending order over consecutive
@@ -170,7 +172,7 @@ __device__ __noinline__ int kth_row(const VT* tile, const uint32_t* dead, int n,
 template <int NW, typename VT>
 __device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, int n,
                                              int lane, const int (&pic)[NW], uint32_t pis,
-                                             uint32_t swarm, uint32_t t, int (&newp)[NW]) {
+                                             uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW]) {
     const int depth = s.depth;
     if (lane < NW) dead[lane] = 0u;
     __syncwarp();
@@ -183,7 +185,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         alive[w] = c < n;
         zal[w] = alive[w];
         ex[w] = false;
-        zv[w] = alive[w] ? VStore<VT>::to_f(tile[pic[w] * n + c]) + 1.0f : 0.0f;
+        zv[w] = alive[w] ? VStore<VT>::to_f(tile[pic[w] * n + c]) + zadd : 0.0f;
         vm[w] = __int_as_float(0x7f800000);
         vc[w] = 0;
         va[w] = -1;
@@ -514,7 +516,9 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int n = s.n;
         const uint32_t t = (uint32_t)*s.t;
         const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
-        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        const bool sx_only = s.sx_only != 0;
+        const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(p / s.ss);
+        const uint32_t pis = sx_only ? (uint32_t)s.sx_pis[p] : (uint32_t)(p % s.ss);
         VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
         // V(t) -> shared memory with one bulk copy (tile padded to 16 bytes)
         __syncwarp();
@@ -527,8 +531,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;
             pic[w] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
-            plc[w] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[w] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+            plc[w] = j < n && !sx_only ? s.PL[(size_t)p * s.ps + j] : -1;
+            pgc[w] = j < n && !sx_only ? s.PG[(size_t)swarm * s.ps + j] : -1;
             newp[w] = 0;
         }
         const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
@@ -541,14 +545,16 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
         const bool newv = s.pos_uses_new_v != 0;
         int ties;
-        if (!newv) {  // Eq. 5 as printed: S_x on X(t) + V(t), then Eq. 4
-            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, newp);
+        if (sx_only) {  // the tile is Y; no velocity
+            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 0.0f, newp);
+        } else if (!newv) {  // Eq. 5 as printed: S_x on X(t) + V(t), then Eq. 4
+            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 1.0f, newp);
             __syncwarp();
             velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, false);
         } else {
             velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, true);
             __syncwarp();
-            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, newp);
+            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 1.0f, newp);
         }
 #pragma unroll
         for (int w = 0; w < NW; ++w) {

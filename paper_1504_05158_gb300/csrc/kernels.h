@@ -75,4 +75,9 @@ int bests_max_swarms();
 cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, int32_t scratch_len,
                          int64_t* out6, double* mean, cudaStream_t st);
 
+// Delta(r, s) of every pair r < s of one permutation (device pointers; out holds
+// n (n - 1) / 2 int64 in r-major pair order).
+cudaError_t launch_delta_table(const int32_t* F, const int32_t* D, int n, const int32_t* perm, int64_t* out,
+                               cudaStream_t st);
+
 }  // namespace qap

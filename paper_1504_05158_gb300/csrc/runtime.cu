@@ -3,6 +3,7 @@
 // state export/import and the single-kernel entry points.
 #include <climits>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -693,6 +694,119 @@ int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t
     if (!inst->sym_zd) return QAP_ERR_UNSUPPORTED;
     if (inst->n > ls_max_n()) return QAP_ERR_UNSUPPORTED;
     return run_ls_hook(inst, perms, count, max_moves, perms, costs, moves, rounds);
+}
+
+int qap_delta_table(qap_instance_t inst, const int32_t* perm, int64_t* out) {
+    if (!inst || !perm || !out) return QAP_ERR_INVALID_ARG;
+    const int n = inst->n;
+    std::vector<char> seen(n, 0);
+    for (int j = 0; j < n; ++j) {
+        if (perm[j] < 0 || perm[j] >= n || seen[perm[j]]) return QAP_ERR_INVALID_ARG;
+        seen[perm[j]] = 1;
+    }
+    // every term is at most 2 max_f max_d in magnitude, 2 n terms
+    if (4.0 * (n + 1) * (double)inst->max_f * (double)inst->max_d >= 9.0e18) return QAP_ERR_OVERFLOW;
+    const size_t npairs = (size_t)n * (n - 1) / 2;
+    int32_t* dp = nullptr;
+    int64_t* dout = nullptr;
+    cudaError_t e = cudaMalloc(&dp, (size_t)n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, npairs * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(dp, perm, (size_t)n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_delta_table(inst->dF, inst->dD, n, dp, dout, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, npairs * 8, cudaMemcpyDeviceToHost);
+    cudaFree(dp);
+    cudaFree(dout);
+    return status_of(e);
+}
+
+int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, const pso_params_t* params,
+                   uint64_t seed, const int32_t* swarm, const int32_t* particle, int32_t t,
+                   int32_t* out_perm) {
+    if (!Y || !Z || !params || !swarm || !particle || !out_perm) return QAP_ERR_INVALID_ARG;
+    if (n < 2 || n > 256 || count < 0 || t < 0) return QAP_ERR_INVALID_ARG;
+    if (params->sx_rule != PSO_SX_ALG1 && params->sx_rule != PSO_SX_TOPD) return QAP_ERR_INVALID_ARG;
+    if (params->depth < 0 || params->depth >= n) return QAP_ERR_INVALID_ARG;
+    if (params->tie_rule != PSO_TIE_RANDOM && params->tie_rule != PSO_TIE_FIRST) return QAP_ERR_INVALID_ARG;
+    if (n > velocity_sx_max_n(0)) return QAP_ERR_UNSUPPORTED;
+    if (count == 0) return QAP_OK;
+    for (int i = 0; i < count; ++i) {
+        if (swarm[i] < 0 || particle[i] < 0) return QAP_ERR_INVALID_ARG;
+        std::vector<char> seen(n, 0);
+        for (int j = 0; j < n; ++j) {
+            const int32_t v = Z[(size_t)i * n + j];
+            if (v < 0 || v >= n || seen[v]) return QAP_ERR_INVALID_ARG;
+            seen[v] = 1;
+        }
+        for (int k = 0; k < n * n; ++k)
+            if (!std::isfinite(Y[(size_t)i * n * n + k])) return QAP_ERR_INVALID_ARG;
+    }
+    // the velocity kernel's layout: 16-byte tiles (bulk copies) and 16-byte permutation rows
+    const size_t vstride = align_up((size_t)n * n, 4);
+    const size_t ps = align_up(n, 16);
+    std::vector<float> hv((size_t)count * vstride, 0.0f);
+    std::vector<uint8_t> hz((size_t)count * ps, 0);
+    for (int i = 0; i < count; ++i) {
+        std::memcpy(hv.data() + (size_t)i * vstride, Y + (size_t)i * n * n, (size_t)n * n * 4);
+        for (int j = 0; j < n; ++j) hz[(size_t)i * ps + j] = (uint8_t)Z[(size_t)i * n + j];
+    }
+    char* base = nullptr;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = align_up(off + b, 256);
+        return o;
+    };
+    const size_t oV = take(hv.size() * 4), oX = take(hz.size()), oS = take(hz.size()),
+                 oSw = take((size_t)count * 4), oPi = take((size_t)count * 4), oT = take(4),
+                 oC = take(CNT_N * 8), oView = take(sizeof(StateView)), oPre = take(8);
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) return status_of(e);
+    StateView sv{};
+    sv.n = n;
+    sv.m = 1;
+    sv.ss = 1;
+    sv.P = count;
+    sv.ps = (int32_t)ps;
+    sv.vstride = (int64_t)vstride;
+    sv.V = base + oV;
+    sv.X = (uint8_t*)(base + oX);
+    sv.Xsx = (uint8_t*)(base + oS);
+    sv.t = (int32_t*)(base + oT);
+    sv.counters = (unsigned long long*)(base + oC);
+    sv.seed = seed;
+    sv.sx_rule = params->sx_rule;
+    sv.depth = params->depth;
+    sv.tie_rule = params->tie_rule;
+    sv.sx_only = 1;
+    sv.sx_swarm = (const int32_t*)(base + oSw);
+    sv.sx_pis = (const int32_t*)(base + oPi);
+    const int32_t prefix[2] = {0, count};
+    auto up = [&](size_t o, const void* src, size_t b) {
+        if (e == cudaSuccess) e = cudaMemcpy(base + o, src, b, cudaMemcpyHostToDevice);
+    };
+    up(oV, hv.data(), hv.size() * 4);
+    up(oX, hz.data(), hz.size());
+    up(oSw, swarm, (size_t)count * 4);
+    up(oPi, particle, (size_t)count * 4);
+    up(oT, &t, 4);
+    up(oView, &sv, sizeof(sv));
+    up(oPre, prefix, sizeof(prefix));
+    if (e == cudaSuccess) e = cudaMemset(base + oC, 0, CNT_N * 8);
+    if (e == cudaSuccess)
+        e = launch_velocity_sx(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
+                                         count, 0, 0},
+                               0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned long long cnt[CNT_N] = {};
+    if (e == cudaSuccess) e = cudaMemcpy(cnt, base + oC, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hz.data(), base + oS, hz.size(), cudaMemcpyDeviceToHost);
+    cudaFree(base);
+    if (e != cudaSuccess) return status_of(e);
+    if (cnt[CNT_ERR]) return QAP_ERR_TIMEOUT;
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < n; ++j) out_perm[(size_t)i * n + j] = hz[(size_t)i * ps + j];
+    return QAP_OK;
 }
 
 }  // extern "C"

@@ -28,6 +28,7 @@ EXPORTS = [
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
     "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
     "pso_batch_size", "pso_batch_member", "pso_batch_destroy", "pso_footprint", "pso_poll",
+    "qap_delta_table", "pso_discretize",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -122,6 +123,9 @@ def lib():
         L.pso_batch_destroy.restype = None
         L.pso_footprint.argtypes = [C.c_int32, C.POINTER(Params), C.POINTER(C.c_size_t)]
         L.pso_poll.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.qap_delta_table.argtypes = [vp, vp, vp]
+        L.pso_discretize.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(Params), C.c_uint64, vp, vp,
+                                     C.c_int32, vp]
         _lib = L
     return _lib
 
@@ -206,6 +210,13 @@ class Instance:
                                       _ptr(rounds)), "qap_local_search")
         return perms, costs, moves, rounds
 
+    def delta_table(self, perm):
+        """Delta(r, s) of every pair r < s of `perm`, r-major (n (n - 1) / 2 int64)."""
+        perm = np.ascontiguousarray(perm, np.int32).reshape(self.n)
+        out = np.zeros(self.n * (self.n - 1) // 2, np.int64)
+        _check(lib().qap_delta_table(self.h, _ptr(perm), _ptr(out)), "qap_delta_table")
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             lib().qap_destroy_instance(self.h)
@@ -216,6 +227,22 @@ class Instance:
             self.close()
         except Exception:
             pass
+
+
+def discretize(Y, Z, params: Params, seed: int, swarm, particle, t: int):
+    """S_x (SecondTarget) of count matrices Y (count x n x n fp32) with Z (count x n
+    permutations); ties draw from the Philox stream of (particle, swarm, t)."""
+    Y = np.ascontiguousarray(Y, np.float32)
+    if Y.ndim == 2:
+        Y = Y[None]
+    count, n = Y.shape[0], Y.shape[1]
+    Z = np.ascontiguousarray(Z, np.int32).reshape(count, n)
+    sw = np.ascontiguousarray(np.broadcast_to(np.asarray(swarm, np.int32), (count,)))
+    pa = np.ascontiguousarray(np.broadcast_to(np.asarray(particle, np.int32), (count,)))
+    out = np.zeros((count, n), np.int32)
+    _check(lib().pso_discretize(_ptr(Y), _ptr(Z), n, count, C.byref(params), seed, _ptr(sw), _ptr(pa), t,
+                                _ptr(out)), "pso_discretize")
+    return out
 
 
 class Swarm:

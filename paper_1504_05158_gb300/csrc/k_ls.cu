@@ -302,47 +302,90 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
 
 // ------------------------------------------------------ tensor-core set-up
 // Teams of WPP warps (1 for n <= 32, 2 for n <= 64, 8 for n <= 128) search one
-// particle at a time, independently of the other teams of the CTA. A team's
-// particle occupies the rows of an M = 128 A tile that sit in the tensor-memory
-// lane quarters of the team's own warps (rows of other quarters are never read
-// back), the team has its own tensor-memory columns and mbarrier, and particles come
-// from a per-population counter, so no team waits for another team's search.
-// KP = NP = n rounded up to 16. The search reads F from its fp16 copy (exact).
+// particle at a time, independently of the other teams of the CTA, taking
+// particles from a per-population counter. Per particle the team keeps, instead
+// of G, the matrix
+//     H[k][m] = G[k][p(m)] - G[k][p(k)]      (zero diagonal)
+// and the permuted distances Dp[k][m] = D[p(k)][p(m)], so that
+//     delta(k, m) = 2 (H[k][m] + H[m][k]) + 4 F[k][m] Dp[k][m]
+// reads four shared-memory words. A swap (r, s) changes G by the rank-1 term
+// fd e^T (fd[k] = F[k][r] - F[k][s], e[x] = Dp[s][x] - Dp[r][x], p before the
+// swap), hence
+//     H[k][m] += fd[k] (e[m] - e[k])                       k, m not in {r, s},
+// rows and columns r, s exchange with their own corrections, and Dp exchanges
+// rows and columns r and s.
+//
+// The set-up is the dense product G_p = F Dp (G_p[k][m] = G[k][p(m)]) on the
+// tensor cores: A = F (shared by every particle of the CTA), B = Dp (per
+// particle; symmetric, so its N x K operand is Dp itself), fp16 operands, fp32
+// accumulation in tensor memory, exact because every term and partial sum is an
+// integer below 2^24. A team's particle occupies the rows of the M = 128
+// accumulator that sit in the tensor-memory lane quarters of its own warps; the
+// A tile holds the n rows of F once, and a team whose quarters start at row
+// `rowbase` points its A descriptor rowbase rows before the tile (those rows of
+// the product are never read back).
 template <int WPP>
 struct TeamLayout {
-    int n, KP, NP, fhs;
-    size_t oD, oFh, oB, oPin, oGd, oPi, oX, oBar, oT, oU, ubytes, total;
+    int n, KP, NP, gs, dps, arows, teams;
+    bool smem_d;
+    size_t tU, tDp, tPi, tFd, tEv, tX, tBar, team_bytes;  // offsets inside a team's block
+    size_t oTeamLo, oA, oTeamHi, oF, oD, oT, total;
 };
 
 constexpr int kXchBytes = 256;  // per team: reduction slots and the next particle
 
+__host__ __device__ inline size_t round128(size_t x) { return (x + 127) & ~size_t(127); }
+
+// two integers (exact in fp16: |v| <= 2048) as a half2 word, a in the low half
+__device__ __forceinline__ uint32_t pack_h2(int a, int b) {
+    return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
+}
+
 template <int WPP>
-__host__ __device__ inline TeamLayout<WPP> team_layout(int n) {
+__host__ __device__ inline TeamLayout<WPP> team_layout(int n, bool allow_smem_d = true) {
     TeamLayout<WPP> L{};
-    constexpr int TEAMS = 8 / WPP;
+    constexpr int TEAMS = WPP == 8 ? 1 : 8;
     L.n = n;
+    L.teams = TEAMS;
     L.KP = round_up(n, 16);
     L.NP = L.KP;
-    L.fhs = round_up(n, 4) + 2;  // odd word stride: column gathers free of bank conflicts
-    size_t o = 0;
-    auto take = [&](size_t b) {
-        const size_t r = o;
-        o = (o + b + 127) & ~size_t(127);
-        return r;
-    };
-    L.oD = take((size_t)n * n * 2);
-    L.oFh = take((size_t)n * L.fhs * 2);
-    L.oB = take((size_t)L.NP * L.KP * 2);
-    L.oPin = take(TEAMS * 128);
-    L.oGd = take(TEAMS * align16((size_t)n * 4));
-    L.oPi = take(TEAMS * align16((size_t)n * 4));
-    L.oX = take(TEAMS * kXchBytes);
-    L.oBar = take(TEAMS * 8);
-    L.oT = take(16);
-    const size_t a_bytes = (size_t)128 * L.KP * 2;
-    L.ubytes = (a_bytes > g_bytes(n) ? a_bytes : g_bytes(n) + 127) & ~size_t(127);
-    L.oU = take((size_t)TEAMS * L.ubytes);
-    L.total = o;
+    L.gs = n | 1;          // odd word stride: column accesses of H free of bank conflicts
+    L.dps = L.KP + 2;      // odd word stride of the uint16 rows of Dp
+    L.arows = WPP >= 4 ? 128 : 32 * WPP;
+    // team block: union(B tile, H), Dp, then the small arrays
+    const size_t b_bytes = (size_t)L.NP * L.KP * 2, h_bytes = (size_t)n * L.gs * 4;
+    L.tU = 0;
+    size_t o = round128(b_bytes > h_bytes ? b_bytes : h_bytes);
+    L.tDp = o;
+    o += round128((size_t)n * L.dps * 2);
+    L.tPi = o;                       // p as bytes, KP entries (zero padded)
+    L.tFd = L.tPi + align16(L.KP);   // int2 per row
+    L.tEv = L.tFd + align16((size_t)n * 8);
+    L.tX = L.tEv + align16((size_t)n * 4);
+    L.tBar = L.tX + kXchBytes;
+    L.team_bytes = round128(L.tBar + 8);
+    // CTA: low teams, A tile, high teams, F, (D), tensor-memory slot. The MMA of a
+    // team reads 128 rows of A from (rowbase rows before) the tile: keep that many
+    // bytes of the allocation on both sides of it.
+    const size_t arow_bytes = (size_t)L.KP * 2;
+    const size_t reach = (size_t)(128 - L.arows) * arow_bytes;
+    const int lo = TEAMS / 2;
+    L.oTeamLo = 0;
+    size_t c = (size_t)lo * L.team_bytes;
+    if (c < reach) c = round128(reach);
+    L.oA = c;
+    c += round128((size_t)L.arows * arow_bytes);
+    L.oTeamHi = c;
+    const size_t after_a = (size_t)(TEAMS - lo) * L.team_bytes;
+    c += after_a > reach ? after_a : round128(reach);
+    L.oF = c;
+    c += round128((size_t)n * n * 2);
+    L.oT = c;
+    c += 128;
+    L.oD = c;
+    L.smem_d = allow_smem_d && c + round128((size_t)n * n * 2) <= kSmemLimit;
+    if (L.smem_d) c += round128((size_t)n * n * 2);
+    L.total = c;
     return L;
 }
 
@@ -414,32 +457,22 @@ __device__ __forceinline__ long long team_sum64(long long v, long long* xch, int
     return t;
 }
 
-__device__ __forceinline__ int fval(const __half* sFh, int fhs, int k, int m) {
-    return __half2int_rn(sFh[k * fhs + m]);
-}
-
-// Best-improvement descent of particle p by one team from a complete G. The team's
+// Best-improvement descent of particle p by one team from a complete H. The team's
 // threads form `nph` phases of `slotw` threads: thread (ph, e) evaluates pair slot e
-// of virtual rows ph, ph + nph, ... and, after a move, updates column e of G in rows
-// ph, ph + nph, ...
+// of virtual rows ph, ph + nph, ... (row t joined with row n-2-t) and, after a move,
+// updates column e of H in rows ph, ph + nph, ...
 template <int WPP>
-__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const __half* sFh, int fhs,
-                                             const uint16_t* sD, int32_t* G, int32_t* gd, int32_t* pi,
-                                             int* xch, int tt, int team) {
+__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const uint16_t* sF, int32_t* H,
+                                             uint16_t* Dp, uint8_t* pi8, int2* fdv, int32_t* ev, int* xch,
+                                             long long cost, int gs, int dps, int tt, int team) {
     constexpr int TT = 32 * WPP;
-    const int n = a.n, gs = n + 1;
+    const int n = a.n;
     const int lane = tt & 31, wi = tt >> 5;
     const int slotw = round_up(n, 32) < TT ? round_up(n, 32) : TT;
     const int nph = TT / slotw, ph = tt / slotw, e = tt % slotw;
     const bool on = ph < nph && e < n;
     const long long npairs = (long long)n * (n - 1) / 2;
     const int nv = n / 2;
-    long long part = 0;
-    for (int m = tt; m < n; m += TT) {
-        gd[m] = G[m * gs + pi[m]];
-        part += gd[m];
-    }
-    long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, wi);
     int moves = 0, rounds = 0;
     if (a.max_moves >= 0) {
         for (;;) {
@@ -448,29 +481,39 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const __hal
                 if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
                 break;
             }
-            int best = INT_MAX;
-            unsigned bkey = 0xFFFFFFFFu;
+            // (delta << 16) | (k << 8 | m): the minimum is the lowest pair on ties; four
+            // independent running minima keep the dependency chains short
+            long long b0 = LLONG_MAX, b1 = LLONG_MAX, b2 = LLONG_MAX, b3 = LLONG_MAX;
             if (on) {
-                for (int t = ph; t < nv; t += nph) {
-                    int k, m;
-                    if (e < n - 1 - t) {
-                        k = t;
-                        m = t + 1 + e;
-                    } else {
-                        k = n - 2 - t;
-                        m = e;
-                        if (k == t) continue;
-                    }
-                    const int pk = pi[k], pmm = pi[m];
-                    const int d = 2 * (G[k * gs + pmm] + G[m * gs + pk] - gd[k] - gd[m]) +
-                                  4 * fval(sFh, fhs, k, m) * (int)sD[pk * n + pmm];
-                    const unsigned key = ((unsigned)k << 8) | (unsigned)m;
-                    if (d < best || (d == best && key < bkey)) {
-                        best = d;
-                        bkey = key;
-                    }
+                auto pair_value = [&](int t) -> long long {
+                    const bool c1 = e < n - 1 - t;
+                    const int k = c1 ? t : n - 2 - t;
+                    const int m = c1 ? t + 1 + e : e;
+                    const int d = 2 * (H[k * gs + m] + H[m * gs + k]) +
+                                  4 * (int)sF[k * n + m] * (int)Dp[k * dps + m];
+                    const long long v = (long long)d * 65536 + ((k << 8) | m);
+                    return (c1 || k != t) ? v : LLONG_MAX;  // k == t: the pair is row t's own
+                };
+                int t = ph;
+                for (; t + 3 * nph < nv; t += 4 * nph) {
+                    const long long v0 = pair_value(t), v1 = pair_value(t + nph);
+                    const long long v2 = pair_value(t + 2 * nph), v3 = pair_value(t + 3 * nph);
+                    b0 = v0 < b0 ? v0 : b0;
+                    b1 = v1 < b1 ? v1 : b1;
+                    b2 = v2 < b2 ? v2 : b2;
+                    b3 = v3 < b3 ? v3 : b3;
+                }
+                for (; t < nv; t += nph) {
+                    const long long v0 = pair_value(t);
+                    b0 = v0 < b0 ? v0 : b0;
                 }
             }
+            b0 = b1 < b0 ? b1 : b0;
+            b2 = b3 < b2 ? b3 : b2;
+            const long long bv = b2 < b0 ? b2 : b0;
+            int best = (int)(bv >> 16);
+            unsigned bkey = bv == LLONG_MAX ? 0xFFFFFFFFu : (unsigned)(bv & 0xFFFF);
+            if (bv == LLONG_MAX) best = INT_MAX;
             team_min2<WPP>(best, bkey, xch, rounds & 1, team, lane, wi);
             ++rounds;
             if (best >= 0) break;
@@ -479,28 +522,73 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const __hal
                 if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
                 break;
             }
-            const int pr = pi[r], pss = pi[s];
-            if (on) {
-                const int bt = (int)sD[pss * n + e] - (int)sD[pr * n + e];
-                for (int k = ph; k < n; k += nph)
-                    G[k * gs + e] += (fval(sFh, fhs, r, k) - fval(sFh, fhs, s, k)) * bt;
+            // A: the move's vectors and the old rows and columns r, s
+            const int Frs = sF[r * n + s], Drs = Dp[r * dps + s];
+            const int hrs = H[r * gs + s], hsr = H[s * gs + r];
+            int fx = 0, ex = 0, drx = 0, dsx = 0, hxr = 0, hxs = 0, hrx = 0, hsx = 0;
+            const int x = tt;
+            if (x < n) {
+                fx = (int)sF[r * n + x] - (int)sF[s * n + x];  // F[x][r] - F[x][s] (symmetric)
+                drx = Dp[r * dps + x];
+                dsx = Dp[s * dps + x];
+                ex = dsx - drx;
+                hxr = H[x * gs + r];
+                hxs = H[x * gs + s];
+                hrx = H[r * gs + x];
+                hsx = H[s * gs + x];
+                fdv[x] = make_int2((x == r || x == s) ? 0 : fx, fx * ex);
+                ev[x] = ex;
             }
-            team_sync<WPP>(team);  // G complete; p itself is still the old one
-            for (int m = tt; m < n; m += TT) {
-                const int pm = m == r ? pss : (m == s ? pr : pi[m]);
-                gd[m] = G[m * gs + pm];
-                if (m == r || m == s) pi[m] = pm;
+            team_sync<WPP>(team);
+            // B: rows and columns outside {r, s}; rows with fd = 0 do not change
+            if (on && e != r && e != s) {
+                const int ec = ev[e];
+                int k = ph;
+                for (; k + 3 * nph < n; k += 4 * nph) {
+                    const int2 q0 = fdv[k], q1 = fdv[k + nph], q2 = fdv[k + 2 * nph], q3 = fdv[k + 3 * nph];
+                    int32_t* h0 = H + k * gs + e;
+                    int32_t* h1 = h0 + nph * gs;
+                    int32_t* h2 = h1 + nph * gs;
+                    int32_t* h3 = h2 + nph * gs;
+                    const int g0 = q0.x ? *h0 : 0, g1 = q1.x ? *h1 : 0, g2 = q2.x ? *h2 : 0, g3 = q3.x ? *h3 : 0;
+                    if (q0.x) *h0 = g0 + q0.x * ec - q0.y;
+                    if (q1.x) *h1 = g1 + q1.x * ec - q1.y;
+                    if (q2.x) *h2 = g2 + q2.x * ec - q2.y;
+                    if (q3.x) *h3 = g3 + q3.x * ec - q3.y;
+                }
+                for (; k < n; k += nph) {
+                    const int2 q = fdv[k];
+                    if (q.x) H[k * gs + e] += q.x * ec - q.y;
+                }
+            }
+            // C: rows and columns r and s (e[r] = Drs, e[s] = -Drs, fd[r] = -Frs, fd[s] = Frs)
+            if (x < n && x != r && x != s) {
+                H[x * gs + r] = hxs - fx * (Drs + ex);
+                H[x * gs + s] = hxr + fx * (Drs - ex);
+                H[r * gs + x] = hrx - hrs - Frs * (ex + Drs);
+                H[s * gs + x] = hsx - hsr + Frs * (ex - Drs);
+                Dp[x * dps + r] = (uint16_t)dsx;
+                Dp[x * dps + s] = (uint16_t)drx;
+                Dp[r * dps + x] = (uint16_t)dsx;
+                Dp[s * dps + x] = (uint16_t)drx;
+            }
+            if (tt == 0) {
+                H[r * gs + s] = -hrs - 2 * Frs * Drs;
+                H[s * gs + r] = -hsr - 2 * Frs * Drs;
+                const uint8_t t8 = pi8[r];
+                pi8[r] = pi8[s];
+                pi8[s] = t8;
             }
             team_sync<WPP>(team);
             cost += best;
             ++moves;
         }
     }
-    for (int m = tt; m < n; m += TT) a.out[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+    for (int m = tt; m < n; m += TT) a.out[(size_t)p * a.ps_out + m] = pi8[m];
     if (a.PL) {
         const long long old = a.costL[p];
         if (cost < old) {
-            for (int m = tt; m < n; m += TT) a.PL[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+            for (int m = tt; m < n; m += TT) a.PL[(size_t)p * a.ps_out + m] = pi8[m];
             if (tt == 0) a.costL[p] = cost;
         }
     }
@@ -522,39 +610,51 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const __hal
     }
 }
 
-// cpi CTAs per population of the table: CTA b serves population b / cpi
+// cpi CTAs per population of the table: CTA b serves population b / cpi. smem_d:
+// D is staged in shared memory (else the Dp gathers read it through the cache).
 template <int WPP>
-__global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args, int cpi) {
+__global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_team(const LsArgs* __restrict__ args, int cpi,
+                                                                  int smem_d) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int TT = 32 * WPP, TEAMS = 8 / WPP;
+    constexpr int TT = 32 * WPP;
     const LsArgs a = args[blockIdx.x / cpi];
     const int cb = blockIdx.x % cpi;
     const int n = a.n;
-    const TeamLayout<WPP> L = team_layout<WPP>(n);
+    const TeamLayout<WPP> L = team_layout<WPP>(n, smem_d != 0);
+    const int TEAMS = L.teams;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int team = warp / WPP, tt = tid - team * TT;
-    uint16_t* sD = reinterpret_cast<uint16_t*>(smem + L.oD);
-    __half* sFh = reinterpret_cast<__half*>(smem + L.oFh);
-    unsigned char* sB = smem + L.oB;
-    uint8_t* pinv = smem + L.oPin + team * 128;
-    int32_t* gd = reinterpret_cast<int32_t*>(smem + L.oGd + team * align16((size_t)n * 4));
-    int32_t* pi = reinterpret_cast<int32_t*>(smem + L.oPi + team * align16((size_t)n * 4));
-    int* xch = reinterpret_cast<int*>(smem + L.oX + team * kXchBytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.oBar) + team;
+    const int lo = TEAMS / 2;
+    unsigned char* tb = smem + (team < lo ? L.oTeamLo + (size_t)team * L.team_bytes
+                                          : L.oTeamHi + (size_t)(team - lo) * L.team_bytes);
+    unsigned char* U = tb + L.tU;
+    int32_t* H = reinterpret_cast<int32_t*>(U);
+    uint16_t* Dp = reinterpret_cast<uint16_t*>(tb + L.tDp);
+    uint8_t* pi8 = tb + L.tPi;
+    int2* fdv = reinterpret_cast<int2*>(tb + L.tFd);
+    int32_t* ev = reinterpret_cast<int32_t*>(tb + L.tEv);
+    int* xch = reinterpret_cast<int*>(tb + L.tX);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tb + L.tBar);
+    unsigned char* sA = smem + L.oA;
+    uint16_t* sF = reinterpret_cast<uint16_t*>(smem + L.oF);
+    const uint16_t* sD = reinterpret_cast<const uint16_t*>(smem + L.oD);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.oT);
-    unsigned char* U = smem + L.oU + (size_t)team * L.ubytes;
-    int32_t* G = reinterpret_cast<int32_t*>(U);
+    const int KP = L.KP, gs = L.gs, dps = L.dps;
 
-    for (int i = tid; i < n * n; i += blockDim.x) sD[i] = (uint16_t)a.D[i];
-    for (int i = tid; i < n * L.fhs; i += blockDim.x) {
-        const int r = i / L.fhs, c = i % L.fhs;
-        sFh[i] = __int2half_rn(c < n ? a.F[r * n + c] : 0);
-    }
-    // B = D (symmetric): row l of the N x K operand is row l of D, zero padded
-    for (int i = tid; i < L.NP * L.KP; i += blockDim.x) {
-        const int l = i / L.KP, j = i % L.KP;
-        const int v = (l < n && j < n) ? a.D[l * n + j] : 0;
-        *reinterpret_cast<__half*>(sB + tc::tile_offset(l, j, L.KP)) = __int2half_rn(v);
+    // shared by every particle: F (uint16, row-major), D when it fits, the A tile
+    // (row i < n holds F[i], rows up to `arows` are zero)
+    for (int i = tid; i < n * n; i += blockDim.x) sF[i] = (uint16_t)a.F[i];
+    if (L.smem_d)
+        for (int i = tid; i < n * n; i += blockDim.x) const_cast<uint16_t*>(sD)[i] = (uint16_t)a.D[i];
+    for (int i = tid; i < L.arows * (KP / 8); i += blockDim.x) {
+        const int r = i / (KP / 8), c = (i % (KP / 8)) * 8;
+        uint32_t h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = c + 2 * q;
+            h[q] = pack_h2(r < n && j < n ? a.F[r * n + j] : 0, r < n && j + 1 < n ? a.F[r * n + j + 1] : 0);
+        }
+        *reinterpret_cast<uint4*>(sA + tc::tile_offset(r, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
     }
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(TEAMS * L.NP)) ncols <<= 1;
@@ -566,10 +666,13 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
     tc::fence_after_sync();
     const uint32_t tcol = *tslot + (uint32_t)(team * L.NP);
     const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
-    const uint32_t sbo = (uint32_t)(L.KP / 8) * 128;
+    const uint32_t sbo = (uint32_t)(KP / 8) * 128;
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
+    const uint32_t a_base = smem_u32(sA) - (uint32_t)(rowbase / 8) * sbo;
     const int wq = warp & 3;                      // this warp's lane quarter
     const bool reader = (warp % WPP) < 4;         // warps that read the team's rows back
+    const int slotw = round_up(n, 32) < TT ? round_up(n, 32) : TT;
+    const int nph = TT / slotw, ph = tt / slotw, col = tt % slotw;
     uint32_t phase = 0;
     int next = cb * TEAMS + team;
     const int stride = cpi * TEAMS;
@@ -586,32 +689,41 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
             next += stride;
         }
         if (p >= a.count) break;
-        for (int m = tt; m < n; m += TT) {
-            const int v = a.in[(size_t)p * a.ps_in + m];
-            pi[m] = v;
-            pinv[v] = (uint8_t)m;
-        }
+        for (int m = tt; m < KP; m += TT) pi8[m] = m < n ? a.in[(size_t)p * a.ps_in + m] : 0;
         team_sync<WPP>(team);
-        // A rows of this particle: row rowbase + k holds F[k][p^-1(j')] in column j'
-        for (int k = tt; k < n; k += TT) {
-            for (int c = 0; c < L.KP; c += 8) {
-                __align__(16) __half h[8];
+        // Dp (uint16 rows) and the B tile (fp16, zero padded) of this particle
+        for (int i = tt; i < L.NP * (KP / 8); i += TT) {
+            const int m = i / (KP / 8), c = (i % (KP / 8)) * 8;
+            uint32_t h[4] = {0u, 0u, 0u, 0u};
+            if (m < n) {
+                const uint2 pj = *reinterpret_cast<const uint2*>(pi8 + c);
+                const int pm = pi8[m];
+                int v[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int j = c + q;
-                    h[q] = j < n ? sFh[k * L.fhs + pinv[j]] : __int2half_rn(0);
+                    const int pjq = (int)(((q < 4 ? pj.x : pj.y) >> (8 * (q & 3))) & 0xFFu);
+                    v[q] = 0;
+                    if (c + q < n) v[q] = L.smem_d ? (int)sD[pm * n + pjq] : __ldg(a.D + pm * n + pjq);
                 }
-                *reinterpret_cast<uint4*>(U + tc::tile_offset(rowbase + k, c, L.KP)) =
-                    *reinterpret_cast<uint4*>(h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
+                    const int j = c + 2 * q;
+                    if (j + 1 < n)
+                        *reinterpret_cast<uint32_t*>(Dp + m * dps + j) = (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
+                    else if (j < n)
+                        Dp[m * dps + j] = (uint16_t)v[2 * q];
+                }
             }
+            *reinterpret_cast<uint4*>(U + tc::tile_offset(m, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
         }
         fence_proxy_async();
         team_sync<WPP>(team);
         if (tt == 0) {
             tc::fence_after_sync();
-            const uint32_t a0 = smem_u32(U), b0 = smem_u32(sB);
-            for (int s = 0; s < L.KP / 16; ++s)
-                tc::mma_f16(tcol, tc::smem_desc(a0 + s * 256, 128, sbo), tc::smem_desc(b0 + s * 256, 128, sbo),
+            const uint32_t b0 = smem_u32(U);
+            for (int s = 0; s < KP / 16; ++s)
+                tc::mma_f16(tcol, tc::smem_desc(a_base + s * 256, 128, sbo), tc::smem_desc(b0 + s * 256, 128, sbo),
                             idesc, s > 0);
             tc::mma_commit(bar);
         }
@@ -622,24 +734,31 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
             break;
         }
         tc::fence_after_sync();
-        // G from tensor memory: reader warp w holds rows k = 32 (w % WPP) + lane of its quarter
+        // G_p from tensor memory (it overwrites the B tile, which the completed
+        // product no longer reads): reader warp w holds rows k = 32 (w % WPP) + lane
         if (reader) {
             const int k = 32 * (warp % WPP) + lane;
             for (int c = 0; c < L.NP; c += 16) {
                 uint32_t v[16];
                 tc::tmem_ld16(tcol + ((uint32_t)(32 * wq) << 16) + (uint32_t)c, v);
                 tc::tmem_wait_ld();
-                // G overwrites the A tile, which the completed product no longer reads
                 if (k < n) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
-                        if (c + q < n) G[k * (n + 1) + c + q] = __float2int_rn(__uint_as_float(v[q]));
+                        if (c + q < n) H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q]));
                 }
             }
+            if (k < n) ev[k] = H[k * gs + k];  // G[k][p(k)]
         }
         tc::fence_before_sync();
         team_sync<WPP>(team);
-        descend_team<WPP>(a, p, sFh, L.fhs, sD, G, gd, pi, xch, tt, team);
+        long long part = 0;
+        for (int m = tt; m < n; m += TT) part += ev[m];
+        const long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, tt >> 5);
+        if (ph < nph && col < n)
+            for (int k = ph; k < n; k += nph) H[k * gs + col] -= ev[k];
+        team_sync<WPP>(team);
+        descend_team<WPP>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
         team_sync<WPP>(team);
     }
     tc::fence_before_sync();
@@ -647,41 +766,59 @@ __global__ void __launch_bounds__(256) k_ls_team(const LsArgs* __restrict__ args
     if (warp == 0) tc::tmem_dealloc(*tslot, ncols);
 }
 
+// CTAs of one launch that fit an SM: shared memory (all of the unified storage as
+// shared memory), threads, and the 512 tensor-memory columns
+template <int WPP>
+int team_ctas_per_sm(const TeamLayout<WPP>& T) {
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    int c = smem_sm / (int)(T.total + reserved);
+    const int threads = 32 * WPP * T.teams;
+    const int by_threads = 2048 / threads;
+    if (c > by_threads) c = by_threads;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_ls_team<WPP>) == cudaSuccess && fa.numRegs > 0) {
+        const int by_regs = 65536 / (fa.numRegs * threads);
+        if (c > by_regs) c = by_regs;
+    }
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(T.teams * T.NP)) ncols <<= 1;
+    if (c > (int)(512 / ncols)) c = (int)(512 / ncols);
+    return c < 1 ? 1 : c;
+}
+
 template <int WPP>
 cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
-    const TeamLayout<WPP> T = team_layout<WPP>(L.n_max);
+    // D in shared memory when it fits, unless reading it through the cache lets
+    // more CTAs share an SM
+    TeamLayout<WPP> T = team_layout<WPP>(L.n_max, true);
+    if (T.smem_d) {
+        const TeamLayout<WPP> T2 = team_layout<WPP>(L.n_max, false);
+        if (team_ctas_per_sm(T2) > team_ctas_per_sm(T)) T = T2;
+    }
     if (T.total > kSmemLimit) return cudaErrorInvalidValue;
+    const int threads = 32 * WPP * T.teams;
     cudaError_t e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)T.total);
-    // all of the unified L1 / shared storage as shared memory, so two CTAs fit an SM
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls_team<WPP>, 256, T.total);
-    int smem_sm = 0, reserved = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    const int by_smem = smem_sm / (int)(T.total + reserved);
-    if (by_smem > per_sm) per_sm = by_smem;  // the occupancy query can ignore the carveout request
-    // co-resident CTAs must fit the 512 tensor-memory columns together
-    uint32_t ncols = 32;
-    while (ncols < (uint32_t)((8 / WPP) * T.NP)) ncols <<= 1;
-    const int tmem_cap = (int)(512 / ncols);
-    if (per_sm > tmem_cap) per_sm = tmem_cap;
-    if (per_sm < 1) per_sm = 1;
+    const int per_sm = team_ctas_per_sm(T);
     int cpi = L.cpi;
     if (cpi <= 0) {  // one wave over the table, at least one CTA per population
         cpi = (sms * per_sm + L.count - 1) / L.count;
-        const int per_pop = (L.total / L.count + (8 / WPP) - 1) / (8 / WPP);
+        const int per_pop = (L.total / L.count + T.teams - 1) / T.teams;
         if (cpi > per_pop) cpi = per_pop;
         if (cpi < 1) cpi = 1;
     }
     e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
     if (e != cudaSuccess) return e;
-    k_ls_team<WPP><<<L.count * cpi, 256, T.total, st>>>(L.d_args, cpi);
+    k_ls_team<WPP><<<L.count * cpi, threads, T.total, st>>>(L.d_args, cpi, T.smem_d ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,12 @@ def workload_config(storage="fp32"):
                         "particles, ring migration every 20 iterations, full swap local search",
             "n": N, "swarms": SWARMS, "swarm_size": SWARM_SIZE, "particles": SWARMS * SWARM_SIZE,
             "v_storage": storage, "sx": "SecondTarget depth 2 (Algorithm 1)", "sv": "Norm",
-            "c": [0.8, 0.5, 0.5], "l2": "flushed before every timed iteration (256 MiB write)"}
+            "c": [0.8, 0.5, 0.5],
+            "l2": ("V (168 MB fp32) is larger than L2: timed iterations back to back"
+                   if storage == "fp32" else "L2 flushed (256 MiB write) before every timed iteration"),
+            "timing": "value: K iterations replayed from the captured CUDA graphs, CUDA events on the "
+                      "state's stream; kernel_ms_per_step: 30 further iterations launched kernel by "
+                      "kernel with events around each, L2 flushed before each"}
 
 
 def params(Q, storage):
@@ -99,12 +104,18 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------- our arm
 
-def algorithmic(n, dmoves, drounds, particles, storage_bytes):
-    """Work of one iteration (see the roofline notes of the design document)."""
+def algorithmic(n, dmoves, drounds, particles, swarms, storage_bytes):
+    """Work of one iteration (the per-unit figures of the design document's roofline
+    notes): velocity bytes (V read and written, X and P^L read, P^G once per swarm),
+    position bytes (V read, X read, S_x result written), local-search integer ops
+    (5 per swap value per round, 2 per entry of the rank-1 update per move) and the
+    set-up's tensor flops (2 n^3 per particle)."""
     npairs = n * (n - 1) // 2
-    k1_bytes = particles * (2 * n * n * storage_bytes + 3 * n)
-    k2_ops = particles * 2 * n ** 3 + drounds * npairs * 10 + dmoves * 2 * n * n
-    return k1_bytes, k2_ops
+    vel_bytes = particles * (2 * n * n * storage_bytes + 2 * n) + swarms * n
+    pos_bytes = particles * (n * n * storage_bytes + 2 * n)
+    ls_ops = drounds * npairs * 5 + dmoves * 2 * n * n
+    ls_tc_flops = particles * 2 * n ** 3
+    return vel_bytes, pos_bytes, ls_ops, ls_tc_flops
 
 
 def measure(Q, W, torch, storage, steps, warmup, rank, flush):
@@ -155,14 +166,33 @@ def run_ours(args, rank, world, local_rank):
         if storage_name not in wanted:
             continue
         sw, s0, stream = measure(Q, W, torch, storage, args.steps, args.warmup, rank, flush)
+        v_bytes = SWARMS * SWARM_SIZE * N * N * (4 if storage == Q.V_FP32 else 2)
+        flush_each = v_bytes <= L2_BYTES  # V larger than L2 needs no flush between iterations
         barrier()
         torch.cuda.synchronize()
+        # timed region: K iterations replayed from the captured graphs (the path a
+        # pso_step caller takes), CUDA events on the state's stream
         with ClockSampler(torch.cuda.current_device() if world == 1 else local_rank) as clk:
-            ms = sw.step_timed(args.steps, flush.data_ptr(), flush.numel())
-        torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                if flush_each:
+                    pairs = []
+                    for _ in range(args.steps):
+                        flush.fill_(1)
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        sw.step(1)
+                        b.record()
+                        pairs.append((a, b))
+                else:
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    sw.step(args.steps)
+                    b.record()
+                    pairs = [(a, b)]
+            torch.cuda.synchronize()
         barrier()
+        span = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
         s1 = sw.stats()
-        span = ms[3] / 1e3
         if dist:
             t = torch.tensor([span], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -170,20 +200,28 @@ def run_ours(args, rank, world, local_rank):
         pits = SWARMS * SWARM_SIZE * args.steps * world
         dfull = s1["delta_full"] - s0["delta_full"]
         dincr = s1["delta_incr"] - s0["delta_incr"]
-        dmoves = s1["ls_moves"] - s0["ls_moves"]
-        drounds = s1["ls_rounds"] - s0["ls_rounds"]
-        k1_bytes, k2_ops = algorithmic(N, dmoves / args.steps, drounds / args.steps,
-                                       SWARMS * SWARM_SIZE, 4 if storage == Q.V_FP32 else 2)
-        k1_ms, k2_ms, k3_ms = (m / args.steps for m in ms[:3])
+        # per-kernel breakdown: further iterations launched one kernel at a time with
+        # events around each (L2 flushed before each iteration, outside the spans)
+        kb = min(args.steps, 30)
+        ms = sw.step_timed(kb, flush.data_ptr(), flush.numel())
+        s2 = sw.stats()
+        dmoves = s2["ls_moves"] - s1["ls_moves"]
+        drounds = s2["ls_rounds"] - s1["ls_rounds"]
+        vel_bytes, pos_bytes, ls_ops, ls_flops = algorithmic(
+            N, dmoves / kb, drounds / kb, SWARMS * SWARM_SIZE, SWARMS, 4 if storage == Q.V_FP32 else 2)
+        pos_ms, ls_ms, bests_ms, _, vel_ms = (m / kb for m in ms)
         best, _, best_it = sw.best()
         results[storage_name] = dict(
             value=pits / span, ms_per_step=span * 1e3 / args.steps,
             delta_evals_per_s=(dfull + dincr) * world / span,
             delta_full_per_s=dfull * world / span, delta_incr_per_s=dincr * world / span,
-            kernel_ms={"velocity_sx": k1_ms, "cost_ls": k2_ms, "bests_migration": k3_ms},
-            k1_gbs=k1_bytes / (k1_ms / 1e3) / 1e9, k2_tops=k2_ops / (k2_ms / 1e3) / 1e12,
-            k1_bytes=k1_bytes, k2_ops=k2_ops,
-            moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * args.steps),
+            kernel_ms={"velocity": vel_ms, "position_sx": pos_ms, "cost_ls": ls_ms,
+                       "bests_migration": bests_ms},
+            vel_gbs=vel_bytes / (vel_ms / 1e3) / 1e9, pos_gbs=pos_bytes / (pos_ms / 1e3) / 1e9,
+            ls_tops=ls_ops / (ls_ms / 1e3) / 1e12, ls_tc_tflops=ls_flops / (ls_ms / 1e3) / 1e12,
+            vel_bytes=vel_bytes, pos_bytes=pos_bytes, ls_ops=ls_ops,
+            moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * kb), flush_each=flush_each,
+            breakdown_iterations=kb,
             best_cost=best, best_iter=best_it, iterations=args.warmup + args.steps,
             clocks=clk.summary())
         sw.close()
@@ -234,16 +272,22 @@ def run_e2e(args, Q, W, torch, dist, rank, world):
 def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
     if True:
         r = results["fp32"]
-        k1, k2 = r["kernel_ms"]["velocity_sx"], r["kernel_ms"]["cost_ls"]
-        if k2 >= k1:
-            roof = {"kernel": "k_ls (goal function + swap local search)", "bound": "alu",
-                    "achieved": r["k2_tops"], "peak": alu_peak_tops, "unit": "Tops/s",
-                    "frac": r["k2_tops"] / alu_peak_tops, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"}
-        else:
-            roof = {"kernel": "k_velocity_sx", "bound": "hbm", "achieved": r["k1_gbs"],
-                    "peak": hbm_peak, "unit": "GB/s", "frac": r["k1_gbs"] / hbm_peak,
-                    "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        km = r["kernel_ms"]
+        roofs = {
+            "cost_ls": {"kernel": "k_ls_team (goal function + swap local search)", "bound": "alu",
+                        "achieved": r["ls_tops"], "peak": alu_peak_tops, "unit": "Tops/s",
+                        "frac": r["ls_tops"] / alu_peak_tops, "traffic": None,
+                        "peak_source": "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"},
+            "position_sx": {"kernel": "k_position (SecondTarget, Algorithm 1)", "bound": "hbm",
+                            "achieved": r["pos_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                            "frac": r["pos_gbs"] / hbm_peak, "traffic": None,
+                            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "velocity": {"kernel": "k_velocity (Eq. 4 + S_v)", "bound": "hbm",
+                         "achieved": r["vel_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                         "frac": r["vel_gbs"] / hbm_peak, "traffic": None,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        }
+        roof = roofs[max(roofs, key=lambda k: km[k])]  # the kernel that takes longest
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
@@ -252,19 +296,17 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
             "delta_evals_per_s": r["delta_evals_per_s"],
             "delta_full_per_s": r["delta_full_per_s"], "delta_incr_per_s": r["delta_incr_per_s"],
             "kernel_ms_per_step": r["kernel_ms"],
-            "hbm_velocity_sx": {"achieved_gbs": r["k1_gbs"], "peak_gbs": hbm_peak,
-                                "frac": r["k1_gbs"] / hbm_peak},
-            "alu_cost_ls": {"achieved_tops": r["k2_tops"], "peak_tops": alu_peak_tops,
-                            "frac": r["k2_tops"] / alu_peak_tops},
             "roofline": roof,
+            "roofline_all": roofs,
+            "ls_setup_tensor_tflops": r["ls_tc_tflops"],
             "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
-                                                       "kernel_ms", "k1_gbs", "best_cost")}
+                                                       "kernel_ms", "vel_gbs", "best_cost")}
                      if "bf16" in results else None),
             "quality": ({"fp32_best": r["best_cost"], "bf16_best": results["bf16"]["best_cost"],
                          "bf16_vs_fp32": results["bf16"]["best_cost"] / r["best_cost"] - 1.0,
                          "iterations": r["iterations"]} if "bf16" in results else None),
             "moves_per_particle_iteration": r["moves_per_pit"],
-            "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": r["clocks"],
+            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
         return line
@@ -352,8 +394,8 @@ def run_batch(args):
                                      "team2 (n<=64)": sum(32 < n <= 64 for n in ns),
                                      "team8 (n<=128)": sum(64 < n <= 128 for n in ns),
                                      "simt (n>128)": sum(n > 128 for n in ns)}},
-           "kernel_ms_per_step": {"velocity_sx": ms[0] / args.steps, "cost_ls": ms[1] / args.steps,
-                                  "bests_migration": ms[2] / args.steps},
+           "kernel_ms_per_step": {"velocity": ms[4] / args.steps, "position_sx": ms[0] / args.steps,
+                                  "cost_ls": ms[1] / args.steps, "bests_migration": ms[2] / args.steps},
            "clocks": clk.summary(), "gpu_launches": None}
     print(json.dumps(out))
     b.close()

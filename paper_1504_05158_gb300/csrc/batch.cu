@@ -100,8 +100,8 @@ cudaError_t autotune(pso_batch* b) {
         for (int w : {1, 2, 4}) {
             VsxLaunch L = b->vsx;
             L.warps = w;
-            if (launch_velocity_sx(L, b->stream) != cudaSuccess) continue;  // warm
-            const float ms = time_on(b->stream, 2, [&] { launch_velocity_sx(L, b->stream); });
+            if (launch_position(L, b->stream) != cudaSuccess) continue;  // warm
+            const float ms = time_on(b->stream, 2, [&] { launch_position(L, b->stream); });
             if (ms < best) {
                 best = ms;
                 pick = w;
@@ -223,8 +223,10 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
         e = cudaMemcpy(d_args, g.host.data(), sizeof(LsArgs) * g.host.size(), cudaMemcpyHostToDevice);
         b->groups.push_back(g);
     }
+    int any_old = 0, any_new = 0;
+    for (int i = 0; i < count; ++i) (params[i].pos_uses_new_v ? any_new : any_old) = 1;
     b->vsx = VsxLaunch{b->d_views, b->d_prefix, count, n_max, total,
-                       params[0].v_storage == PSO_V_BF16, 0};
+                       params[0].v_storage == PSO_V_BF16, 0, any_old, any_new};
     if (e == cudaSuccess && autotune_shapes) {
         e = autotune(b);
         // the tuning runs advanced the members: start them again from their seeds
@@ -261,40 +263,10 @@ int pso_batch_step(pso_batch_t b, int32_t iterations) {
 int pso_batch_step_timed(pso_batch_t b, int32_t iterations, void* flush_buf, size_t flush_bytes,
                          float* ms_out) {
     if (!b || iterations < 0 || !ms_out) return QAP_ERR_INVALID_ARG;
-    if (iterations == 0) return QAP_OK;
-    std::vector<cudaEvent_t> ev((size_t)iterations * 4, nullptr);
-    cudaError_t e = cudaSuccess;
-    for (auto& x : ev)
-        if (e == cudaSuccess) e = cudaEventCreate(&x);
-    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        cudaEvent_t* q = &ev[(size_t)i * 4];
-        if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[0], b->stream);
-        if (e == cudaSuccess) e = launch_velocity_sx(b->vsx, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[1], b->stream);
-        for (auto& g : b->groups)
-            if (e == cudaSuccess) e = launch_ls(g.launch, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[2], b->stream);
-        if (e == cudaSuccess) e = launch_bests(b->d_views, (int)b->members.size(), b->m_max, 0, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[3], b->stream);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {  // velocity, search, bests
-            float ms = 0.f;
-            e = cudaEventElapsedTime(&ms, ev[(size_t)i * 4 + k], ev[(size_t)i * 4 + k + 1]);
-            acc[k] += ms;
-        }
-        float span = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&span, ev[(size_t)i * 4], ev[(size_t)i * 4 + 3]);
-        acc[3] += span;
-    }
-    for (auto& x : ev)
-        if (x) cudaEventDestroy(x);
-    if (e != cudaSuccess) return status_of(e);
-    for (int k = 0; k < 4; ++k) ms_out[k] += acc[k];
-    return QAP_OK;
+    std::vector<LsLaunch> ls;
+    for (auto& g : b->groups) ls.push_back(g.launch);
+    const TimedParts T{&b->vsx, ls.data(), (int)ls.size(), b->d_views, (int)b->members.size(), b->m_max};
+    return status_of(timed_iterations(b->stream, iterations, flush_buf, flush_bytes, T, ms_out));
 }
 
 int pso_batch_member(pso_batch_t b, int32_t index, pso_state_t* out) {

@@ -106,6 +106,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// shared -> global bulk copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned), committed as one bulk group of the issuing thread
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// waits until the issuing thread's bulk stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// waits until the issuing thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // waits for phase `parity` of `bar` to complete; gives up after a bounded number of
 // polls and returns false (the caller records an error instead of hanging)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {

@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include "kernels.h"
+#include "launch.cuh"
 #include "tc.cuh"
 
 namespace qap {
@@ -770,19 +771,14 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
 // shared memory), threads, and the 512 tensor-memory columns
 template <int WPP>
 int team_ctas_per_sm(const TeamLayout<WPP>& T) {
-    int dev = 0, smem_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    int smem_sm = 0, reserved = 0;
+    smem_limits(&smem_sm, &reserved);
     int c = smem_sm / (int)(T.total + reserved);
     const int threads = 32 * WPP * T.teams;
     const int by_threads = 2048 / threads;
     if (c > by_threads) c = by_threads;
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, k_ls_team<WPP>) == cudaSuccess && fa.numRegs > 0) {
-        const int by_regs = 65536 / (fa.numRegs * threads);
-        if (c > by_regs) c = by_regs;
-    }
+    const int regs = kernel_regs<k_ls_team<WPP>>();
+    if (regs > 0 && c > 65536 / (regs * threads)) c = 65536 / (regs * threads);
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(T.teams * T.NP)) ncols <<= 1;
     if (c > (int)(512 / ncols)) c = (int)(512 / ncols);
@@ -800,14 +796,9 @@ cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
     }
     if (T.total > kSmemLimit) return cudaErrorInvalidValue;
     const int threads = 32 * WPP * T.teams;
-    cudaError_t e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)T.total);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ls_team<WPP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = configure_once<k_ls_team<WPP>>();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     const int per_sm = team_ctas_per_sm(T);
     int cpi = L.cpi;
     if (cpi <= 0) {  // one wave over the table, at least one CTA per population
@@ -829,15 +820,10 @@ cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
     while (wpc > 1 && shared_part(n) + wpc * warp_part(n) > kSmemLimit) --wpc;
     const size_t smem = shared_part(n) + wpc * warp_part(n);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_ls<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_ls<NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = configure_once<k_ls<NW>>();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ls<NW>, wpc * 32, smem);
+    const int sms = sm_count();
+    int per_sm = occupancy_cached<k_ls<NW>>(wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int cpi = L.cpi;
     if (cpi <= 0) {

@@ -1,5 +1,6 @@
-// Initialisation and the velocity/position update of every particle, one warp
-// per particle, the particle's n x n velocity tile staged in shared memory.
+// Initialisation, the velocity update and the position update of every particle,
+// one warp per particle: the velocity kernel streams V through global memory, the
+// position kernel stages the particle's n x n tile in shared memory.
 //
 // Velocity (section 3.1, Eq. 4): W = c1 V(t) + c2 r2 (P^L - X(t)) + c3 r3 (P^G - X(t)),
 // V(t+1) = S_v(W); S_v Raw clamps to [-v_max, v_max], Norm then divides column j by
@@ -19,6 +20,7 @@
 #include <climits>
 
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace qap {
 namespace {
@@ -294,6 +296,10 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
                     if (!alive[w] || vc[w] == 0) continue;  // rows of the round are never pic[w]
+                    if (vc[w] == 1) {  // its only copy is row va: gone iff va was deleted
+                        if ((dead[va[w] >> 5] >> (va[w] & 31)) & 1u) vc[w] = 0;
+                        continue;
+                    }
                     const int c = lane + 32 * w;
 #pragma unroll
                     for (int wi = 0; wi < NW; ++wi) {
@@ -431,71 +437,230 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
     return ties;
 }
 
-// Eq. 4 with S_v for one particle: reads V(t) from the tile, writes V(t+1) to global
-// memory and, when the position uses it (pos_uses_new_v), back into the tile. With
-// fp32 storage the unnormalised W is kept in the tile between the two passes.
+// The flat particle index f of a table of populations: the population and the
+// particle inside it (f only grows along a warp's grid-stride loop).
+struct TableCursor {
+    int inst = 0;
+    __device__ __forceinline__ int advance(const int32_t* prefix, int count, int f) {
+        while (inst + 1 < count && prefix[inst + 1] <= f) ++inst;
+        return f - prefix[inst];
+    }
+};
+
+// Velocity (Eq. 4 + S_v) of every particle of the table whose position update uses
+// V(t+1) (phase 1) or V(t) (phase 0). One CTA of kVelWarps warps per particle: one
+// thread brings the tile of the CTA's next particle into shared memory with a bulk
+// copy while the warps update the current one (two buffers), so several tiles are
+// in flight per SM and V is read from memory once. Warp w takes rows w, w +
+// kVelWarps, ... of the lane's columns j = lane + 32 c; Norm adds the warps' partial
+// column sums in shared memory in a fixed order; V(t+1) is stored from registers.
+constexpr int kVelWarps = 8;
+
 template <int NW, typename VT>
-__device__ __forceinline__ void velocity(const StateView& s, VT* tile, VT* Vg, int n, int lane, const int (&pic)[NW],
-                         const int (&plc)[NW], const int (&pgc)[NW], float a, float b, bool newv) {
-    const bool norm = s.sv_kind == 1;
-    constexpr bool kInPlace = sizeof(VT) == 4;
-    float sum[NW];
+__global__ void __launch_bounds__(kVelWarps * 32)
+    k_velocity(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int phase,
+               int n_max) {
+    constexpr int R = (32 * NW + kVelWarps - 1) / kVelWarps;  // rows per warp for n <= 32 NW
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ float part[kVelWarps][32 * NW];
+    __shared__ float inv_s[32 * NW];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const size_t tb_max = tile_bytes<VT>(n_max);
+    const int total = prefix[count];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+    }
+    __syncthreads();
+    TableCursor look;
+    auto next_active = [&](int f) {  // the CTA's next particle of this phase
+        for (; f < total; f += gridDim.x) {
+            look.advance(prefix, count, f);
+            const StateView& v = views[look.inst];
+            if (((v.pos_uses_new_v != 0) == (phase != 0)) && !v.sx_only) break;
+        }
+        return f;
+    };
+    auto issue = [&](int f, int slot) {  // thread 0: the bulk load of particle f's tile
+        const StateView& v = views[look.inst];
+        fence_proxy_async();
+        bulk_load(smem + (size_t)slot * tb_max,
+                  reinterpret_cast<const VT*>(v.V) + (size_t)(f - prefix[look.inst]) * v.vstride,
+                  (uint32_t)tile_bytes<VT>(v.n), bar + slot);
+    };
+    int f = next_active(blockIdx.x);
+    if (f < total && tid == 0) issue(f, 0);
+    uint32_t par0 = 0u, par1 = 0u;
+    int slot = 0;
+    TableCursor cur;
+    while (f < total) {
+        const int p = cur.advance(prefix, count, f);
+        const StateView s = views[cur.inst];
+        const int fn = next_active(f + gridDim.x);
+        if (fn < total && tid == 0) issue(fn, slot ^ 1);  // its buffer was released below
+        const int n = s.n;
+        const uint32_t t = (uint32_t)*s.t;
+        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        int pic[NW], plc[NW], pgc[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) sum[w] = 0.0f;
-    for (int i = 0; i < n; ++i) {
+        for (int c = 0; c < NW; ++c) {
+            const int j = lane + 32 * c;
+            pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
+            plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
+            pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+        }
+        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
+        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
+        const bool norm = s.sv_kind == 1;
+        const bool ok = __syncthreads_and(mbar_wait(bar + slot, slot ? par1 : par0));
+        if (slot)
+            par1 ^= 1u;
+        else
+            par0 ^= 1u;
+        if (!ok) {  // the copy never landed: record, stop this CTA
+            if (tid == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            return;
+        }
+        const VT* tile = reinterpret_cast<const VT*>(smem + (size_t)slot * tb_max);
+        auto wval = [&](int i, int c) {
+            const float v = VStore<VT>::to_f(tile[i * n + lane + 32 * c]);
+            const float dl = (float)((plc[c] == i) - (pic[c] == i));
+            const float dg = (float)((pgc[c] == i) - (pic[c] == i));
+            return fminf(fmaxf(fmaf(s.c1, v, a * dl + b * dg), -s.v_max), s.v_max);
+        };
+        if (norm) {
+            float sum[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int j = lane + 32 * w;
-            if (j < n) {
-                const float v = VStore<VT>::to_f(tile[i * n + j]);
-                const float dl = (float)((plc[w] == i) - (pic[w] == i));
-                const float dg = (float)((pgc[w] == i) - (pic[w] == i));
-                float x = fmaf(s.c1, v, a * dl + b * dg);
-                x = fminf(fmaxf(x, -s.v_max), s.v_max);
-                if (norm) {
-                    sum[w] += fabsf(x);
-                    if (kInPlace) tile[i * n + j] = VStore<VT>::from_f(x);
-                } else {
-                    const VT o = VStore<VT>::from_f(x);
-                    Vg[i * n + j] = o;
-                    if (newv) tile[i * n + j] = o;
+            for (int c = 0; c < NW; ++c) sum[c] = 0.0f;
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int i = warp + kVelWarps * u;
+#pragma unroll
+                for (int c = 0; c < NW; ++c)
+                    if (i < n && lane + 32 * c < n) sum[c] += fabsf(wval(i, c));
+            }
+#pragma unroll
+            for (int c = 0; c < NW; ++c) part[warp][lane + 32 * c] = sum[c];
+            __syncthreads();
+            for (int j = tid; j < 32 * NW; j += blockDim.x) {
+                float tsum = 0.0f;
+#pragma unroll
+                for (int w = 0; w < kVelWarps; ++w) tsum += part[w][j];
+                inv_s[j] = tsum > 0.0f ? 1.0f / tsum : 1.0f;
+            }
+            __syncthreads();
+        }
+        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            const int j = lane + 32 * c;
+            const float iv = norm ? inv_s[j] : 1.0f;
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int i = warp + kVelWarps * u;
+                if (i < n && j < n) {
+                    const float x = wval(i, c);
+                    Vg[i * n + j] = VStore<VT>::from_f(norm ? x * iv : x);
                 }
             }
         }
+        __syncthreads();  // the tile, part and inv_s are free for the next particles
+        slot ^= 1;
+        f = fn;
     }
-    if (!norm) return;
-    float inv[NW];
+}
+
+// The same for n > 128: one warp per particle, rows streamed in batches of RB whose
+// loads are issued before any use; Norm reads the rows twice (the second read
+// mostly hits L2).
+template <int NW, typename VT>
+__global__ void __launch_bounds__(128)
+    k_velocity_wide(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count,
+                    int phase) {
+    constexpr int RB = 2;
+    const int wpc = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = prefix[count];
+    TableCursor cur;
+    for (int f = blockIdx.x * wpc + warp; f < total; f += gridDim.x * wpc) {
+        const int p = cur.advance(prefix, count, f);
+        const StateView s = views[cur.inst];
+        if ((s.pos_uses_new_v != 0) != (phase != 0) || s.sx_only) continue;
+        const int n = s.n;
+        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+        const uint32_t t = (uint32_t)*s.t;
+        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        int pic[NW], plc[NW], pgc[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) inv[w] = sum[w] > 0.0f ? 1.0f / sum[w] : 1.0f;
-    for (int i = 0; i < n; ++i) {
+        for (int c = 0; c < NW; ++c) {
+            const int j = lane + 32 * c;
+            pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
+            plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
+            pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+        }
+        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
+        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
+        const bool norm = s.sv_kind == 1;
+        auto wval = [&](int i, int c, float x0) {
+            const float dl = (float)((plc[c] == i) - (pic[c] == i));
+            const float dg = (float)((pgc[c] == i) - (pic[c] == i));
+            return fminf(fmaxf(fmaf(s.c1, x0, a * dl + b * dg), -s.v_max), s.v_max);
+        };
+        float inv[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int j = lane + 32 * w;
-            if (j < n) {
-                float x;
-                if (kInPlace) {
-                    x = VStore<VT>::to_f(tile[i * n + j]);
-                } else {
-                    const float v = VStore<VT>::to_f(tile[i * n + j]);
-                    const float dl = (float)((plc[w] == i) - (pic[w] == i));
-                    const float dg = (float)((pgc[w] == i) - (pic[w] == i));
-                    x = fmaf(s.c1, v, a * dl + b * dg);
-                    x = fminf(fmaxf(x, -s.v_max), s.v_max);
-                }
-                const VT o = VStore<VT>::from_f(x * inv[w]);
-                Vg[i * n + j] = o;
-                if (newv) tile[i * n + j] = o;
+        for (int c = 0; c < NW; ++c) inv[c] = 1.0f;
+        if (norm) {
+            float sum[NW];
+#pragma unroll
+            for (int c = 0; c < NW; ++c) sum[c] = 0.0f;
+            for (int i0 = 0; i0 < n; i0 += RB) {
+                float v[RB][NW];
+#pragma unroll
+                for (int u = 0; u < RB; ++u)
+#pragma unroll
+                    for (int c = 0; c < NW; ++c) {
+                        const int i = i0 + u, j = lane + 32 * c;
+                        v[u][c] = (i < n && j < n) ? VStore<VT>::to_f(Vg[i * n + j]) : 0.0f;
+                    }
+#pragma unroll
+                for (int u = 0; u < RB; ++u)
+#pragma unroll
+                    for (int c = 0; c < NW; ++c)
+                        if (i0 + u < n && lane + 32 * c < n) sum[c] += fabsf(wval(i0 + u, c, v[u][c]));
             }
+#pragma unroll
+            for (int c = 0; c < NW; ++c) inv[c] = sum[c] > 0.0f ? 1.0f / sum[c] : 1.0f;
+        }
+        for (int i0 = 0; i0 < n; i0 += RB) {
+            float v[RB][NW];
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+#pragma unroll
+                for (int c = 0; c < NW; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    v[u][c] = (i < n && j < n) ? VStore<VT>::to_f(Vg[i * n + j]) : 0.0f;
+                }
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+#pragma unroll
+                for (int c = 0; c < NW; ++c) {
+                    const int i = i0 + u, j = lane + 32 * c;
+                    if (i < n && j < n) {
+                        const float x = wval(i, c, v[u][c]);
+                        Vg[i * n + j] = VStore<VT>::from_f(norm ? x * inv[c] : x);
+                    }
+                }
         }
     }
 }
 
-// Covers a table of populations: flat particle index f over all of them (prefix
-// offsets), shared-memory slots sized for the largest n of the table.
+// Position (Eq. 5, S_x = SecondTarget) of every particle of the table: the V tile
+// (V(t), or V(t+1) already written by the velocity kernel) is staged in shared memory
+// with one bulk copy; shared-memory slots are sized for the largest n of the table.
 template <int NW, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
-    k_velocity_sx(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count,
-                  int n_max) {
+    k_position(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max) {
     const int wpc = blockDim.x >> 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -507,55 +672,41 @@ __global__ void __launch_bounds__(kWarps * 32)
     __syncwarp();
     uint32_t phase = 0;
     const int total = prefix[count];
-    int inst = 0;
+    TableCursor cur;
 
     for (int f = blockIdx.x * wpc + warp; f < total; f += gridDim.x * wpc) {
-        while (inst + 1 < count && prefix[inst + 1] <= f) ++inst;  // f only grows
-        const StateView s = views[inst];
-        const int p = f - prefix[inst];
+        const int p = cur.advance(prefix, count, f);
+        const StateView s = views[cur.inst];
         const int n = s.n;
         const uint32_t t = (uint32_t)*s.t;
         const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
         const bool sx_only = s.sx_only != 0;
         const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(p / s.ss);
         const uint32_t pis = sx_only ? (uint32_t)s.sx_pis[p] : (uint32_t)(p % s.ss);
-        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
-        // V(t) -> shared memory with one bulk copy (tile padded to 16 bytes)
+        const VT* Vg = reinterpret_cast<const VT*>(s.V) + (size_t)p * s.vstride;
+        // the tile -> shared memory with one bulk copy (tile padded to 16 bytes)
         __syncwarp();
         if (lane == 0) {
             fence_proxy_async();
             bulk_load(tile, Vg, tbytes, bar);
         }
-        int pic[NW], plc[NW], pgc[NW], newp[NW];
+        int pic[NW], newp[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;
             pic[w] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
-            plc[w] = j < n && !sx_only ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[w] = j < n && !sx_only ? s.PG[(size_t)swarm * s.ps + j] : -1;
             newp[w] = 0;
         }
-        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
         const bool ok = mbar_wait(bar, phase);
         phase ^= 1u;
         if (!__all_sync(FULL, ok)) {  // the copy never landed: record, leave this warp
             if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
             return;
         }
-        const bool newv = s.pos_uses_new_v != 0;
-        int ties;
-        if (sx_only) {  // the tile is Y; no velocity
-            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 0.0f, newp);
-        } else if (!newv) {  // Eq. 5 as printed: S_x on X(t) + V(t), then Eq. 4
-            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 1.0f, newp);
-            __syncwarp();
-            velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, false);
-        } else {
-            velocity<NW, VT>(s, tile, Vg, n, lane, pic, plc, pgc, a, b, true);
-            __syncwarp();
-            ties = second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, 1.0f, newp);
-        }
+        // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
+        // the discretisation entry point
+        const int ties =
+            second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, sx_only ? 0.0f : 1.0f, newp);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;
@@ -567,41 +718,77 @@ __global__ void __launch_bounds__(kWarps * 32)
 }
 
 template <int NW, typename VT>
-cudaError_t launch_vsx(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_pos(const VsxLaunch& L, cudaStream_t st) {
     int wpc = L.warps > 0 ? L.warps : kWarps;  // warps (particles) per CTA
     if (wpc > kWarps) wpc = kWarps;
     while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(L.n_max) > kSmemLimit) --wpc;
     const size_t smem = kBarBytes + wpc * warp_bytes<VT>(L.n_max);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_velocity_sx<NW, VT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = configure_once<k_position<NW, VT>>();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_velocity_sx<NW, VT>, wpc * 32, smem);
+    const int sms = sm_count();
+    int per_sm = occupancy_cached<k_position<NW, VT>>(wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     const int need = (L.total + wpc - 1) / wpc;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_velocity_sx<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max);
+    k_position<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max);
+    return cudaGetLastError();
+}
+
+template <int NW, typename VT>
+cudaError_t launch_vel(const VsxLaunch& L, int phase, cudaStream_t st) {
+    const int sms = sm_count();
+    int per_sm = 0;
+    if constexpr (NW <= 4) {
+        const size_t smem = 2 * tile_bytes<VT>(L.n_max);
+        if (smem > kSmemLimit - 8 * 1024) return cudaErrorInvalidValue;
+        cudaError_t e = configure_once<k_velocity<NW, VT>>();
+        if (e != cudaSuccess) return e;
+        per_sm = occupancy_cached<k_velocity<NW, VT>>(kVelWarps * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        int grid = sms * per_sm;
+        if (grid > L.total) grid = L.total;
+        k_velocity<NW, VT><<<grid, kVelWarps * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, phase, L.n_max);
+    } else {
+        constexpr int kWide = 4;
+        per_sm = occupancy_cached<k_velocity_wide<NW, VT>>(kWide * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        int grid = sms * per_sm;
+        const int need = (L.total + kWide - 1) / kWide;
+        if (grid > need) grid = need;
+        k_velocity_wide<NW, VT><<<grid, kWide * 32, 0, st>>>(L.d_views, L.d_prefix, L.count, phase);
+    }
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t launch_vsx_t(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_pos_t(const VsxLaunch& L, cudaStream_t st) {
     switch ((L.n_max + 31) / 32) {
-        case 1: return launch_vsx<1, VT>(L, st);
-        case 2: return launch_vsx<2, VT>(L, st);
-        case 3: return launch_vsx<3, VT>(L, st);
-        case 4: return launch_vsx<4, VT>(L, st);
-        case 5: return launch_vsx<5, VT>(L, st);
+        case 1: return launch_pos<1, VT>(L, st);
+        case 2: return launch_pos<2, VT>(L, st);
+        case 3: return launch_pos<3, VT>(L, st);
+        case 4: return launch_pos<4, VT>(L, st);
+        case 5: return launch_pos<5, VT>(L, st);
         case 6:
         case 7:
-        case 8: return launch_vsx<8, VT>(L, st);
+        case 8: return launch_pos<8, VT>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename VT>
+cudaError_t launch_vel_t(const VsxLaunch& L, int phase, cudaStream_t st) {
+    switch ((L.n_max + 31) / 32) {
+        case 1: return launch_vel<1, VT>(L, phase, st);
+        case 2: return launch_vel<2, VT>(L, phase, st);
+        case 3: return launch_vel<3, VT>(L, phase, st);
+        case 4: return launch_vel<4, VT>(L, phase, st);
+        case 5: return launch_vel<5, VT>(L, phase, st);
+        case 6: return launch_vel<6, VT>(L, phase, st);
+        case 7: return launch_vel<7, VT>(L, phase, st);
+        case 8: return launch_vel<8, VT>(L, phase, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -629,10 +816,23 @@ cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_position(const VsxLaunch& L, cudaStream_t st) {
     if (L.total <= 0) return cudaSuccess;
     if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
-    return L.v_bf16 ? launch_vsx_t<__nv_bfloat16>(L, st) : launch_vsx_t<float>(L, st);
+    return L.v_bf16 ? launch_pos_t<__nv_bfloat16>(L, st) : launch_pos_t<float>(L, st);
+}
+
+cudaError_t launch_velocity(const VsxLaunch& L, int phase, cudaStream_t st) {
+    if (L.total <= 0 || !(phase ? L.has_new_v : L.has_old_v)) return cudaSuccess;
+    if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
+    return L.v_bf16 ? launch_vel_t<__nv_bfloat16>(L, phase, st) : launch_vel_t<float>(L, phase, st);
+}
+
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
+    cudaError_t e = launch_velocity(L, 1, st);
+    if (e == cudaSuccess) e = launch_position(L, st);
+    if (e == cudaSuccess) e = launch_velocity(L, 0, st);
+    return e;
 }
 
 }  // namespace qap

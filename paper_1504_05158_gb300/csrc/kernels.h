@@ -51,7 +51,8 @@ struct LsLaunch {
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st);
 int ls_max_n();
 
-// One velocity + S_x launch over `count` populations (flat index over particles).
+// The velocity and position launches over `count` populations (flat index over
+// particles).
 struct VsxLaunch {
     const StateView* d_views;
     const int32_t* d_prefix;  // count + 1 particle offsets
@@ -59,8 +60,15 @@ struct VsxLaunch {
     int n_max;
     int total;                // prefix[count]
     int v_bf16;               // every population of the table has the same storage
-    int warps;                // warps per CTA (0 = automatic)
+    int warps;                // warps per CTA of the position kernel (0 = automatic)
+    int has_old_v;            // some population forms X(t) + V(t) (velocity after S_x)
+    int has_new_v;            // some population forms X(t) + V(t+1) (velocity first)
 };
+// S_x of every particle (reads the V tiles, writes Xsx)
+cudaError_t launch_position(const VsxLaunch& L, cudaStream_t st);
+// Eq. 4 for the populations of the phase (1: pos_uses_new_v, 0: the others)
+cudaError_t launch_velocity(const VsxLaunch& L, int phase, cudaStream_t st);
+// velocity (phase 1), position, velocity (phase 0): one iteration's update
 cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st);
 int velocity_sx_max_n(int v_bf16);
 

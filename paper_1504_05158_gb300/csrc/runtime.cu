@@ -90,6 +90,50 @@ cudaError_t reinit_state(pso_state* s, cudaStream_t st) {
     return e;
 }
 
+cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
+                             const TimedParts& T, float* ms_out) {
+    if (iterations <= 0) return cudaSuccess;
+    constexpr int E = 6;  // [vel(new V)] pos [vel(old V)] search bests
+    std::vector<cudaEvent_t> ev((size_t)iterations * E, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
+        cudaEvent_t* q = &ev[(size_t)i * E];
+        if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[0], st);
+        if (e == cudaSuccess) e = launch_velocity(*T.vsx, 1, st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[1], st);
+        if (e == cudaSuccess) e = launch_position(*T.vsx, st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[2], st);
+        if (e == cudaSuccess) e = launch_velocity(*T.vsx, 0, st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[3], st);
+        for (int g = 0; g < T.nls && e == cudaSuccess; ++g) e = launch_ls(T.ls[g], st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[4], st);
+        if (e == cudaSuccess) e = launch_bests(T.views, T.count, T.m_max, 0, st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[5], st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    auto span = [&](int i, int a, int b) {
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[(size_t)i * E + a], ev[(size_t)i * E + b]);
+        return ms;
+    };
+    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
+        acc[0] += span(i, 1, 2);
+        acc[1] += span(i, 3, 4);
+        acc[2] += span(i, 4, 5);
+        acc[3] += span(i, 0, 5);
+        acc[4] += span(i, 0, 1) + span(i, 2, 3);
+    }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e == cudaSuccess)
+        for (int k = 0; k < 5; ++k) ms_out[k] += acc[k];
+    return e;
+}
+
 }  // namespace qap
 
 namespace {
@@ -314,7 +358,8 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     s->h_ls[1] = ls_args_for(s, true, s->d_work + 1);
     s->h_prefix[0] = 0;
     s->h_prefix[1] = P;
-    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0};
+    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0,
+                       params->pos_uses_new_v ? 0 : 1, params->pos_uses_new_v ? 1 : 0};
     s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     e = cudaMemsetAsync(base, 0, off, s->stream);
@@ -383,39 +428,8 @@ int pso_step(pso_state_t s, int32_t iterations) {
 int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t flush_bytes,
                    float* ms_out) {
     if (!s || iterations < 0 || !ms_out) return QAP_ERR_INVALID_ARG;
-    if (iterations == 0) return QAP_OK;
-    std::vector<cudaEvent_t> ev((size_t)iterations * 4, nullptr);
-    cudaError_t e = cudaSuccess;
-    for (auto& x : ev)
-        if (e == cudaSuccess) e = cudaEventCreate(&x);
-    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        cudaEvent_t* q = &ev[(size_t)i * 4];
-        if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, s->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[0], s->stream);
-        if (e == cudaSuccess) e = launch_velocity_sx(s->vsx, s->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[1], s->stream);
-        if (e == cudaSuccess) e = launch_ls(s->ls_iter, s->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[2], s->stream);
-        if (e == cudaSuccess) e = launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(q[3], s->stream);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-            float ms = 0.f;
-            e = cudaEventElapsedTime(&ms, ev[(size_t)i * 4 + k], ev[(size_t)i * 4 + k + 1]);
-            acc[k] += ms;
-        }
-        float span = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&span, ev[(size_t)i * 4], ev[(size_t)i * 4 + 3]);
-        acc[3] += span;
-    }
-    for (auto& x : ev)
-        if (x) cudaEventDestroy(x);
-    if (e != cudaSuccess) return status_of(e);
-    for (int k = 0; k < 4; ++k) ms_out[k] += acc[k];
-    return QAP_OK;
+    const TimedParts T{&s->vsx, &s->ls_iter, 1, s->d_view, 1, s->sv.m};
+    return status_of(timed_iterations(s->stream, iterations, flush_buf, flush_bytes, T, ms_out));
 }
 
 int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
@@ -794,9 +808,9 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     up(oPre, prefix, sizeof(prefix));
     if (e == cudaSuccess) e = cudaMemset(base + oC, 0, CNT_N * 8);
     if (e == cudaSuccess)
-        e = launch_velocity_sx(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
-                                         count, 0, 0},
-                               0);
+        e = launch_position(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
+                                      count, 0, 0, 0, 0},
+                            0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     unsigned long long cnt[CNT_N] = {};
     if (e == cudaSuccess) e = cudaMemcpy(cnt, base + oC, sizeof(cnt), cudaMemcpyDeviceToHost);

@@ -43,6 +43,21 @@ struct pso_state {
 };
 
 namespace qap {
+// The launches of one iteration, for timing them one by one.
+struct TimedParts {
+    const VsxLaunch* vsx;
+    const LsLaunch* ls;
+    int nls;
+    const StateView* views;
+    int count;
+    int m_max;
+};
+// Runs `iterations` iterations with events around every phase (after writing
+// flush_bytes of flush_buf, when given) and adds the device milliseconds to ms_out:
+// [0] position (S_x), [1] goal function + local search, [2] bests + migration,
+// [3] whole iterations, [4] velocity.
+cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
+                             const TimedParts& T, float* ms_out);
 int status_of(cudaError_t e);
 LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work);
 cudaError_t reinit_state(pso_state* s, cudaStream_t st);

@@ -267,11 +267,11 @@ class Swarm:
 
     def step_timed(self, iterations=1, flush_ptr=None, flush_bytes=0):
         """Runs iterations with per-kernel device times; returns milliseconds of
-        [velocity + S_x, goal function + local search, bests + migration, span]."""
-        ms = (C.c_float * 4)()
+        [position S_x, goal function + local search, bests + migration, span, velocity]."""
+        ms = (C.c_float * 5)()
         fp = C.c_void_p(flush_ptr) if flush_ptr else None
         _check(lib().pso_step_timed(self.h, iterations, fp, flush_bytes, ms), "pso_step_timed")
-        return [ms[0], ms[1], ms[2], ms[3]]
+        return list(ms)
 
     def done(self):
         """True when all work queued on this population's stream has finished."""
@@ -360,10 +360,10 @@ class Batch:
         _check(lib().pso_batch_step(self.h, iterations), "pso_batch_step")
 
     def step_timed(self, iterations=1, flush_ptr=None, flush_bytes=0):
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 5)()
         fp = C.c_void_p(flush_ptr) if flush_ptr else None
         _check(lib().pso_batch_step_timed(self.h, iterations, fp, flush_bytes, ms), "pso_batch_step_timed")
-        return [ms[0], ms[1], ms[2], ms[3]]
+        return list(ms)
 
     def close(self):
         if getattr(self, "h", None):

@@ -104,6 +104,25 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------- our arm
 
+# DRAM bytes (read + write) of one launch of each kernel on this workload, from one
+# ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum); set to None
+# when the kernel changes
+PROFILED_TRAFFIC = {"cost_ls": 814592, "position_sx": 168487936 + 4124928,
+                    "velocity": 169230848 + 107718656}
+
+
+def aggregate(units, span_s, dist, torch, device):
+    """Whole-job figures of a multi-rank run: the units every rank processed (summed)
+    and the slowest rank's time (max); one rank returns its own."""
+    if not dist:
+        return units, span_s
+    t = torch.tensor([span_s], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return int(u.item()), float(t.item())
+
+
 def algorithmic(n, dmoves, drounds, particles, swarms, storage_bytes):
     """Work of one iteration (the per-unit figures of the design document's roofline
     notes): velocity bytes (V read and written, X and P^L read, P^G once per swarm),
@@ -193,11 +212,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         span = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
         s1 = sw.stats()
-        if dist:
-            t = torch.tensor([span], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            span = float(t.item())
-        pits = SWARMS * SWARM_SIZE * args.steps * world
+        pits, span = aggregate(SWARMS * SWARM_SIZE * args.steps, span, dist, torch, "cuda")
         dfull = s1["delta_full"] - s0["delta_full"]
         dincr = s1["delta_incr"] - s0["delta_incr"]
         # per-kernel breakdown: further iterations launched one kernel at a time with
@@ -259,11 +274,8 @@ def run_e2e(args, Q, W, torch, dist, rank, world):
     e2e_s = time.perf_counter() - t0
     sw.close()
     gi.close()
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    return {"value": SWARMS * SWARM_SIZE * args.steps * world / e2e_s, "unit": UNIT,
+    units, e2e_s = aggregate(SWARMS * SWARM_SIZE * args.steps, e2e_s, dist, torch, "cuda")
+    return {"value": units / e2e_s, "unit": UNIT,
             "h2d_bytes_per_step": 2 * N * N * 4 / args.steps,
             "d2h_bytes_per_step": 8 + 4 + N,
             "what": "qap_create_instance + pso_init + K x (pso_step(1) + pso_best), host F and D"}
@@ -276,15 +288,15 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
         roofs = {
             "cost_ls": {"kernel": "k_ls_team (goal function + swap local search)", "bound": "alu",
                         "achieved": r["ls_tops"], "peak": alu_peak_tops, "unit": "Tops/s",
-                        "frac": r["ls_tops"] / alu_peak_tops, "traffic": None,
+                        "frac": r["ls_tops"] / alu_peak_tops, "traffic": PROFILED_TRAFFIC["cost_ls"],
                         "peak_source": "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"},
             "position_sx": {"kernel": "k_position (SecondTarget, Algorithm 1)", "bound": "hbm",
                             "achieved": r["pos_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                            "frac": r["pos_gbs"] / hbm_peak, "traffic": None,
+                            "frac": r["pos_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["position_sx"],
                             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "velocity": {"kernel": "k_velocity (Eq. 4 + S_v)", "bound": "hbm",
                          "achieved": r["vel_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                         "frac": r["vel_gbs"] / hbm_peak, "traffic": None,
+                         "frac": r["vel_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["velocity"],
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         }
         roof = roofs[max(roofs, key=lambda k: km[k])]  # the kernel that takes longest

@@ -121,6 +121,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // waits for phase `parity` of `bar` to complete; gives up after a bounded number of
 // polls and returns false (the caller records an error instead of hanging)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t sleep_ns = 32;
     for (int it = 0; it < (1 << 22); ++it) {
         uint32_t ok;
         asm volatile(
@@ -129,7 +130,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (it > 64) __nanosleep(64);
+        if (it >= 4) {  // back off: leave the issue slots to other warps
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 256) sleep_ns <<= 1;
+        }
     }
     return false;
 }

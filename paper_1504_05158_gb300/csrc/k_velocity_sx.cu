@@ -37,7 +37,7 @@ __host__ __device__ inline size_t tile_bytes(int n) {
 }
 template <typename VT>
 __host__ __device__ inline size_t warp_bytes(int n) {
-    return tile_bytes<VT>(n) + 32;  // + deleted-row bits (8 words)
+    return tile_bytes<VT>(n) + 96;  // + deleted-row bits (8 words) + the tail's row/column lists
 }
 
 // --------------------------------------------------------------------- init
@@ -160,6 +160,110 @@ __device__ __noinline__ int kth_row(const VT* tile, const uint32_t* dead, int n,
     return -1;
 }
 
+// The last steps of SecondTarget once at most kTailCols columns are left and the
+// exclusion phase is over: the remaining A x A cells (at most kTailSlots per lane)
+// run the greedy directly, one maximum and one ballot count per step. Cells are
+// numbered q = (column index) A + (row index) over the remaining columns and rows,
+// both ascending, which is the column-major order of M that the tie draw uses.
+constexpr int kTailSlots = 4;
+constexpr int kTailCols = 11;  // kTailCols^2 <= 32 kTailSlots
+
+template <int NW, typename VT>
+__device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const uint32_t* dead, uint8_t* lists,
+                                       int n, int lane, const int (&pic)[NW], const bool (&alive)[NW],
+                                       uint32_t pis, uint32_t swarm, uint32_t t, float zadd, int step, int A,
+                                       int (&newp)[NW]) {
+    uint8_t* rows = lists;       // remaining rows, ascending
+    uint8_t* cols = lists + 16;  // remaining columns, ascending
+    uint8_t* xrow = lists + 32;  // their X(t) rows
+    const unsigned below_me = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int wi = 0; wi < NW; ++wi) {
+        const int lim = n - 32 * wi;  // rows of this word (none past n when NW is wider than n needs)
+        uint32_t m = lim <= 0 ? 0u : ~dead[wi];
+        if (lim > 0 && lim < 32) m &= (1u << lim) - 1u;
+        if ((m >> lane) & 1u) rows[base + __popc(m & below_me)] = (uint8_t)(32 * wi + lane);
+        base += __popc(m);
+    }
+    base = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const unsigned am = __ballot_sync(FULL, alive[w]);
+        if (alive[w]) {
+            const int pos = base + __popc(am & below_me);
+            cols[pos] = (uint8_t)(lane + 32 * w);
+            xrow[pos] = (uint8_t)pic[w];
+        }
+        base += __popc(am);
+    }
+    __syncwarp();
+    uint32_t key[kTailSlots];
+    int rc[kTailSlots];  // (row index << 8) | column index
+#pragma unroll
+    for (int sl = 0; sl < kTailSlots; ++sl) {
+        const int q = lane + 32 * sl;
+        key[sl] = 0u;  // no cell (every finite value has a nonzero key)
+        rc[sl] = 0;
+        if (q < A * A) {
+            const int ci = q / A, ri = q % A;
+            const int r = rows[ri], c = cols[ci];
+            float y = VStore<VT>::to_f(tile[r * n + c]);
+            if (r == xrow[ci]) y += zadd;
+            key[sl] = fkey(y);
+            rc[sl] = (ri << 8) | ci;
+        }
+    }
+    int ties = 0;
+    for (int k = 0; k < A; ++k, ++step) {
+        uint32_t lm = 0u;
+#pragma unroll
+        for (int sl = 0; sl < kTailSlots; ++sl) lm = max(lm, key[sl]);
+        const uint32_t gm = __reduce_max_sync(FULL, lm);
+        unsigned b[kTailSlots];
+        int tot = 0;
+#pragma unroll
+        for (int sl = 0; sl < kTailSlots; ++sl) {
+            b[sl] = __ballot_sync(FULL, key[sl] != 0u && key[sl] == gm);
+            tot += __popc(b[sl]);
+        }
+        int kk = 0;
+        if (tot > 1) {
+            ++ties;
+            if (s.tie_rule == 0) {
+                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                kk = (int)below(word_of(u, step & 3), (uint32_t)tot);
+            }
+        }
+        // the kk-th cell of M in cell order (slot, then lane)
+        int src = 0, val = 0;
+        bool found = false;
+#pragma unroll
+        for (int sl = 0; sl < kTailSlots; ++sl) {
+            const int c = __popc(b[sl]);
+            if (!found && kk < c) {
+                unsigned m = b[sl];
+                for (int j = 0; j < kk; ++j) m &= m - 1u;  // drop the kk lower members
+                src = __ffs(m) - 1;
+                val = rc[sl];
+                found = true;
+            } else if (!found) {
+                kk -= c;
+            }
+        }
+        const int pick = __shfl_sync(FULL, val, src);
+        const int ri = pick >> 8, ci = pick & 0xFF;
+        const int r = rows[ri], c = cols[ci];
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (lane + 32 * w == c) newp[w] = r;
+#pragma unroll
+        for (int sl = 0; sl < kTailSlots; ++sl)
+            if ((rc[sl] >> 8) == ri || (rc[sl] & 0xFF) == ci) key[sl] = 0u;
+    }
+    return ties;
+}
+
 // SecondTarget (Algorithm 1) on Y for one particle; returns the number of steps
 // whose set M had more than one element and leaves the location chosen for each
 // owned column (facility) in newp. The tile holds V with Y = X(t) + V (zadd = 1:
@@ -220,13 +324,28 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         }
     }
     int ties = 0;
+    // A round can only form after the greedy has just taken an X(t) cell (or at the
+    // first step past the exclusion phase, or right after a round): when it takes a
+    // plain cell instead, every X(t) cell was below the largest plain value, so the
+    // test is skipped (single steps give the same result in every case).
+    bool try_round = true;
     for (int step = 0; step < n;) {
         const bool use_ex = step < depth;
+        if (!use_ex) {
+            int A = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) A += __popc(__ballot_sync(FULL, alive[w]));
+            if (A <= kTailCols) {
+                ties += sx_tail<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic, alive,
+                                        pis, swarm, t, zadd, step, A, newp);
+                break;
+            }
+        }
         bool zin[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) zin[w] = alive[w] && zal[w] && !(use_ex && ex[w]);
 
-        if (!use_ex) {
+        if (!use_ex && try_round) {
             // ---- a round of X(t) cells above every remaining plain value ----
 #pragma unroll
             for (int w = 0; w < NW; ++w)
@@ -357,23 +476,32 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
         for (int w = 0; w < NW; ++w) lm = max(lm, key[w]);
         const uint32_t gm = __reduce_max_sync(FULL, lm);
-        int lc = 0;
+        // |M| = 1 iff exactly one column holds the maximum, once
+        unsigned hit[NW];
+        int nhit = 0;
+        bool multi = false;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) lc += (key[w] == gm) ? cnt[w] : 0;
-        const int tot = (int)__reduce_add_sync(FULL, (unsigned)lc);
+        for (int w = 0; w < NW; ++w) {
+            hit[w] = __ballot_sync(FULL, key[w] == gm);
+            nhit += __popc(hit[w]);
+            multi = multi || (key[w] == gm && cnt[w] > 1);
+        }
+        const bool unique = nhit == 1 && !__any_sync(FULL, multi);
         // the column holding the k-th element of M (columns c = lane + 32 w ascending)
         int owner = -1, ow = 0, kk = 0;
-        if (tot == 1) {
+        if (unique) {
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                if (owner >= 0) continue;
-                const unsigned bal = __ballot_sync(FULL, key[w] == gm);
-                if (bal) {
-                    owner = __ffs(bal) - 1;
+                if (owner < 0 && hit[w]) {
+                    owner = __ffs(hit[w]) - 1;
                     ow = w;
                 }
             }
         } else {
+            int lc = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) lc += (key[w] == gm) ? cnt[w] : 0;
+            const int tot = (int)__reduce_add_sync(FULL, (unsigned)lc);
             int k = 0;
             ++ties;
             if (s.tie_rule == 0) {
@@ -402,7 +530,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             }
         }
         // the owner takes the kk-th row (ascending) holding its column's maximum
-        int r = -1;
+        int r = -1, took_x = 0;
         if (lane == owner) {
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
@@ -412,14 +540,17 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                     r = kth_row<VT>(tile, dead, n, lane + 32 * w, pic[w], zin[w], zv[w], vm[w], kk);
                 newp[w] = r;
                 alive[w] = false;
+                took_x = (zin[w] && r == pic[w]) ? 1 : 0;
+                if (r >= 0 && r < n) dead[r >> 5] |= 1u << (r & 31);
             }
         }
-        r = __shfl_sync(FULL, r, owner < 0 ? 0 : owner);
+        const int rx = __shfl_sync(FULL, (r & 0xFFFF) | (took_x << 16), owner < 0 ? 0 : owner);
+        r = (int)(short)(rx & 0xFFFF);
+        if (!use_ex) try_round = (rx >> 16) != 0;
         if (owner < 0 || r < 0 || r >= n) {  // cannot happen; never index with it
             if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
             return ties;
         }
-        if (lane == 0) dead[r >> 5] |= 1u << (r & 31);
         __syncwarp();
         // the other columns lose row r
 #pragma unroll
@@ -464,6 +595,7 @@ __global__ void __launch_bounds__(kVelWarps * 32)
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ float part[kVelWarps][32 * NW];
     __shared__ float inv_s[32 * NW];
+    __shared__ float ab_s[2][2];  // c2 r2 and c3 r3 of the particle of each buffer
     __shared__ __align__(8) uint64_t bar[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const size_t tb_max = tile_bytes<VT>(n_max);
@@ -494,11 +626,14 @@ __global__ void __launch_bounds__(kVelWarps * 32)
     uint32_t par0 = 0u, par1 = 0u;
     int slot = 0;
     TableCursor cur;
+    // thread 0: the updated tile of the previous particle, stored by one bulk copy
+    // once every warp has written it (after the next CTA barrier)
+    VT* pend_dst = nullptr;
+    uint32_t pend_bytes = 0;
     while (f < total) {
         const int p = cur.advance(prefix, count, f);
         const StateView s = views[cur.inst];
         const int fn = next_active(f + gridDim.x);
-        if (fn < total && tid == 0) issue(fn, slot ^ 1);  // its buffer was released below
         const int n = s.n;
         const uint32_t t = (uint32_t)*s.t;
         const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
@@ -510,24 +645,59 @@ __global__ void __launch_bounds__(kVelWarps * 32)
             plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
             pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
         }
-        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
+        if (tid == 0) {  // one draw per particle, shared through shared memory
+            const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
+            ab_s[slot][0] = s.c2 * u01f(ur.x);
+            ab_s[slot][1] = s.c3 * u01f(ur.y);
+        }
         const bool norm = s.sv_kind == 1;
-        const bool ok = __syncthreads_and(mbar_wait(bar + slot, slot ? par1 : par0));
+        // one warp waits for the tile; the CTA barrier passes it on (and orders every
+        // warp's reads of the other buffer, from the previous particle, before its refill)
+        bool landed = true;
+        if (warp == 0) landed = mbar_wait(bar + slot, slot ? par1 : par0);
+        const bool ok = __syncthreads_and(landed);
+        const float a = ab_s[slot][0], b = ab_s[slot][1];
         if (slot)
             par1 ^= 1u;
         else
             par0 ^= 1u;
         if (!ok) {  // the copy never landed: record, stop this CTA
-            if (tid == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            if (tid == 0) {
+                atomicAdd(s.counters + CNT_ERR, 1ull);
+                bulk_wait_all();
+            }
             return;
         }
-        const VT* tile = reinterpret_cast<const VT*>(smem + (size_t)slot * tb_max);
+        if (tid == 0) {
+            if (pend_dst) {
+                fence_proxy_async();
+                bulk_store(pend_dst, smem + (size_t)(slot ^ 1) * tb_max, pend_bytes);
+                pend_dst = nullptr;
+            }
+            if (fn < total) {
+                bulk_wait_read();  // the store has read the buffer the next tile goes to
+                issue(fn, slot ^ 1);
+            }
+        }
+        VT* tile = reinterpret_cast<VT*>(smem + (size_t)slot * tb_max);
+        // W at a cell: c1 v + a dl + b dg, clamped; dl and dg vanish outside the rows
+        // X(t), P^L and P^G of the column, where W is clamp(c1 v) (the same fp32 value:
+        // fmaf(c1, v, 0) rounds like c1 * v)
+        auto wgen = [&](float v) { return fminf(fmaxf(s.c1 * v, -s.v_max), s.v_max); };
         auto wval = [&](int i, int c) {
             const float v = VStore<VT>::to_f(tile[i * n + lane + 32 * c]);
             const float dl = (float)((plc[c] == i) - (pic[c] == i));
             const float dg = (float)((pgc[c] == i) - (pic[c] == i));
             return fminf(fmaxf(fmaf(s.c1, v, a * dl + b * dg), -s.v_max), s.v_max);
+        };
+        // the distinct special rows of column c owned by this warp: row i of the tile
+        // belongs to warp i mod kVelWarps
+        auto special = [&](int c, int q) {  // q = 0, 1, 2: X(t), P^L, P^G row, or -1
+            const int i = q == 0 ? pic[c] : (q == 1 ? plc[c] : pgc[c]);
+            if (i < 0 || i % kVelWarps != warp) return -1;
+            if (q >= 1 && i == pic[c]) return -1;
+            if (q == 2 && i == plc[c]) return -1;
+            return i;
         };
         if (norm) {
             float sum[NW];
@@ -538,7 +708,17 @@ __global__ void __launch_bounds__(kVelWarps * 32)
                 const int i = warp + kVelWarps * u;
 #pragma unroll
                 for (int c = 0; c < NW; ++c)
-                    if (i < n && lane + 32 * c < n) sum[c] += fabsf(wval(i, c));
+                    if (i < n && lane + 32 * c < n) sum[c] += fabsf(wgen(VStore<VT>::to_f(tile[i * n + lane + 32 * c])));
+            }
+#pragma unroll
+            for (int c = 0; c < NW; ++c) {
+                if (lane + 32 * c >= n) continue;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const int i = special(c, q);
+                    if (i >= 0)
+                        sum[c] += fabsf(wval(i, c)) - fabsf(wgen(VStore<VT>::to_f(tile[i * n + lane + 32 * c])));
+                }
             }
 #pragma unroll
             for (int c = 0; c < NW; ++c) part[warp][lane + 32 * c] = sum[c];
@@ -551,23 +731,45 @@ __global__ void __launch_bounds__(kVelWarps * 32)
             }
             __syncthreads();
         }
-        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+        // V(t+1) into the tile in place: the special rows from V(t) first, then every
+        // row with the generic value, then the special rows again
 #pragma unroll
         for (int c = 0; c < NW; ++c) {
             const int j = lane + 32 * c;
+            if (j >= n) continue;
             const float iv = norm ? inv_s[j] : 1.0f;
+            float sx[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int i = special(c, q);
+                sx[q] = i >= 0 ? wval(i, c) : 0.0f;
+            }
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const int i = warp + kVelWarps * u;
-                if (i < n && j < n) {
-                    const float x = wval(i, c);
-                    Vg[i * n + j] = VStore<VT>::from_f(norm ? x * iv : x);
+                if (i < n) {
+                    const float x = wgen(VStore<VT>::to_f(tile[i * n + j]));
+                    tile[i * n + j] = VStore<VT>::from_f(norm ? x * iv : x);
                 }
             }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int i = special(c, q);
+                if (i >= 0) tile[i * n + j] = VStore<VT>::from_f(norm ? sx[q] * iv : sx[q]);
+            }
         }
-        __syncthreads();  // the tile, part and inv_s are free for the next particles
-        slot ^= 1;
+        fence_proxy_async();  // this thread's tile writes, before the bulk store reads them
+        if (tid == 0) {
+            pend_dst = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+            pend_bytes = (uint32_t)tile_bytes<VT>(n);
+        }
+        slot ^= 1;  // the next particle's barrier frees this tile, part and inv_s
         f = fn;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (pend_dst) bulk_store(pend_dst, smem + (size_t)(slot ^ 1) * tb_max, pend_bytes);
+        bulk_wait_all();
     }
 }
 

@@ -183,7 +183,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
         m_max = std::max(m_max, (int)s->sv.m);
     }
     b->m_max = m_max;
-    int kind_count[LS_KINDS] = {0, 0, 0, 0};
+    int kind_count[LS_KINDS] = {};
     for (auto* s : b->members) ++kind_count[s->ls_iter.kind];
     size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024;
     for (int k = 0; k < LS_KINDS; ++k) bytes += (sizeof(LsArgs) + sizeof(int32_t)) * kind_count[k] + 512;

@@ -15,12 +15,10 @@
 // so a round costs O(1) per pair after an O(n^3) set-up per iteration.
 //
 // The set-up G = F * D_p is a dense product. Two kernels form it:
-//   k_ls_team (n <= 128, symmetric, entries <= 2048, n max_f max_d < 2^24): on the
-//     tensor cores (tcgen05, fp16 operands, fp32 accumulation in tensor memory).
-//     Every operand and partial sum is an integer below 2^24, so the fp32 result is
-//     exact. With G[k][l] = sum_j' F[k][p^-1(j')] D[j'][l], the A operand is F with
-//     its columns gathered by p^-1 (one particle per M = 128 tile) and the B operand
-//     is D itself (symmetric, shared by every particle).
+//   k_ls_team (symmetric, entries <= 2048, n max_f max_d < 2^24; n <= 128, or
+//     n <= 160 with entries <= 255): on the tensor cores (tcgen05, fp16 operands,
+//     fp32 accumulation in tensor memory). Every operand and partial sum is an
+//     integer below 2^24, so the fp32 result is exact (details at the kernel).
 //   k_ls (any n up to the shared-memory limit): integer multiply-adds on the SIMT
 //     cores.
 // Layout: F (int32, rows padded to fs) and D (uint16) are staged once per CTA in
@@ -325,9 +323,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
 // A tile holds the n rows of F once, and a team whose quarters start at row
 // `rowbase` points its A descriptor rowbase rows before the tile (those rows of
 // the product are never read back).
-template <int WPP>
+template <int WPP, typename ET>
 struct TeamLayout {
-    int n, KP, NP, gs, dps, arows, teams;
+    int n, KP, NP, gs, dps, arows, mrows, groups, teams;
     bool smem_d;
     size_t tU, tDp, tPi, tFd, tEv, tX, tBar, team_bytes;  // offsets inside a team's block
     size_t oTeamLo, oA, oTeamHi, oF, oD, oT, total;
@@ -342,23 +340,27 @@ __device__ __forceinline__ uint32_t pack_h2(int a, int b) {
     return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
 }
 
-template <int WPP>
-__host__ __device__ inline TeamLayout<WPP> team_layout(int n, bool allow_smem_d = true) {
-    TeamLayout<WPP> L{};
+template <int WPP, typename ET>
+__host__ __device__ inline TeamLayout<WPP, ET> team_layout(int n, bool allow_smem_d = true) {
+    TeamLayout<WPP, ET> L{};
     constexpr int TEAMS = WPP == 8 ? 1 : 8;
+    constexpr int ES = (int)sizeof(ET);
     L.n = n;
     L.teams = TEAMS;
     L.KP = round_up(n, 16);
     L.NP = L.KP;
-    L.gs = n | 1;          // odd word stride: column accesses of H free of bank conflicts
-    L.dps = L.KP + 2;      // odd word stride of the uint16 rows of Dp
-    L.arows = WPP >= 4 ? 128 : 32 * WPP;
+    L.gs = n | 1;            // odd word stride: column accesses of H free of bank conflicts
+    L.dps = L.KP + 4 / ES;   // odd word stride of the rows of Dp
+    // accumulator rows: one M = 128 product, two past 128 rows (A rows 128.. second)
+    L.groups = n > 128 ? 2 : 1;
+    L.mrows = 128 * L.groups;
+    L.arows = WPP >= 4 ? (n > 128 ? L.KP : 128) : 32 * WPP;
     // team block: union(B tile, H), Dp, then the small arrays
     const size_t b_bytes = (size_t)L.NP * L.KP * 2, h_bytes = (size_t)n * L.gs * 4;
     L.tU = 0;
     size_t o = round128(b_bytes > h_bytes ? b_bytes : h_bytes);
     L.tDp = o;
-    o += round128((size_t)n * L.dps * 2);
+    o += round128((size_t)n * L.dps * ES);
     L.tPi = o;                       // p as bytes, KP entries (zero padded)
     L.tFd = L.tPi + align16(L.KP);   // int2 per row
     L.tEv = L.tFd + align16((size_t)n * 8);
@@ -369,7 +371,8 @@ __host__ __device__ inline TeamLayout<WPP> team_layout(int n, bool allow_smem_d 
     // team reads 128 rows of A from (rowbase rows before) the tile: keep that many
     // bytes of the allocation on both sides of it.
     const size_t arow_bytes = (size_t)L.KP * 2;
-    const size_t reach = (size_t)(128 - L.arows) * arow_bytes;
+    const size_t reach = (size_t)(128 - (L.arows < 128 ? L.arows : 128)) * arow_bytes;  // before A
+    const size_t reach_after = (size_t)(L.mrows - L.arows) * arow_bytes;               // after A's rows
     const int lo = TEAMS / 2;
     L.oTeamLo = 0;
     size_t c = (size_t)lo * L.team_bytes;
@@ -378,14 +381,14 @@ __host__ __device__ inline TeamLayout<WPP> team_layout(int n, bool allow_smem_d 
     c += round128((size_t)L.arows * arow_bytes);
     L.oTeamHi = c;
     const size_t after_a = (size_t)(TEAMS - lo) * L.team_bytes;
-    c += after_a > reach ? after_a : round128(reach);
+    c += after_a > reach_after ? after_a : round128(reach_after);
     L.oF = c;
-    c += round128((size_t)n * n * 2);
+    c += round128((size_t)n * n * ES);
     L.oT = c;
     c += 128;
     L.oD = c;
-    L.smem_d = allow_smem_d && c + round128((size_t)n * n * 2) <= kSmemLimit;
-    if (L.smem_d) c += round128((size_t)n * n * 2);
+    L.smem_d = allow_smem_d && c + round128((size_t)n * n * ES) <= kSmemLimit;
+    if (L.smem_d) c += round128((size_t)n * n * ES);
     L.total = c;
     return L;
 }
@@ -462,10 +465,10 @@ __device__ __forceinline__ long long team_sum64(long long v, long long* xch, int
 // threads form `nph` phases of `slotw` threads: thread (ph, e) evaluates pair slot e
 // of virtual rows ph, ph + nph, ... (row t joined with row n-2-t) and, after a move,
 // updates column e of H in rows ph, ph + nph, ...
-template <int WPP>
-__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const uint16_t* sF, int32_t* H,
-                                             uint16_t* Dp, uint8_t* pi8, int2* fdv, int32_t* ev, int* xch,
-                                             long long cost, int gs, int dps, int tt, int team) {
+template <int WPP, typename ET>
+__device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* sF, int32_t* H, ET* Dp,
+                                             uint8_t* pi8, int2* fdv, int32_t* ev, int* xch, long long cost,
+                                             int gs, int dps, int tt, int team) {
     constexpr int TT = 32 * WPP;
     const int n = a.n;
     const int lane = tt & 31, wi = tt >> 5;
@@ -568,10 +571,10 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const uint1
                 H[x * gs + s] = hxr + fx * (Drs - ex);
                 H[r * gs + x] = hrx - hrs - Frs * (ex + Drs);
                 H[s * gs + x] = hsx - hsr + Frs * (ex - Drs);
-                Dp[x * dps + r] = (uint16_t)dsx;
-                Dp[x * dps + s] = (uint16_t)drx;
-                Dp[r * dps + x] = (uint16_t)dsx;
-                Dp[s * dps + x] = (uint16_t)drx;
+                Dp[x * dps + r] = (ET)dsx;
+                Dp[x * dps + s] = (ET)drx;
+                Dp[r * dps + x] = (ET)dsx;
+                Dp[s * dps + x] = (ET)drx;
             }
             if (tt == 0) {
                 H[r * gs + s] = -hrs - 2 * Frs * Drs;
@@ -613,15 +616,15 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const uint1
 
 // cpi CTAs per population of the table: CTA b serves population b / cpi. smem_d:
 // D is staged in shared memory (else the Dp gathers read it through the cache).
-template <int WPP>
-__global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_team(const LsArgs* __restrict__ args, int cpi,
-                                                                  int smem_d) {
+template <int WPP, typename ET>
+__global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
+    k_ls_team(const LsArgs* __restrict__ args, int cpi, int smem_d) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int TT = 32 * WPP;
     const LsArgs a = args[blockIdx.x / cpi];
     const int cb = blockIdx.x % cpi;
     const int n = a.n;
-    const TeamLayout<WPP> L = team_layout<WPP>(n, smem_d != 0);
+    const TeamLayout<WPP, ET> L = team_layout<WPP, ET>(n, smem_d != 0);
     const int TEAMS = L.teams;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int team = warp / WPP, tt = tid - team * TT;
@@ -630,23 +633,23 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
                                           : L.oTeamHi + (size_t)(team - lo) * L.team_bytes);
     unsigned char* U = tb + L.tU;
     int32_t* H = reinterpret_cast<int32_t*>(U);
-    uint16_t* Dp = reinterpret_cast<uint16_t*>(tb + L.tDp);
+    ET* Dp = reinterpret_cast<ET*>(tb + L.tDp);
     uint8_t* pi8 = tb + L.tPi;
     int2* fdv = reinterpret_cast<int2*>(tb + L.tFd);
     int32_t* ev = reinterpret_cast<int32_t*>(tb + L.tEv);
     int* xch = reinterpret_cast<int*>(tb + L.tX);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tb + L.tBar);
     unsigned char* sA = smem + L.oA;
-    uint16_t* sF = reinterpret_cast<uint16_t*>(smem + L.oF);
-    const uint16_t* sD = reinterpret_cast<const uint16_t*>(smem + L.oD);
+    ET* sF = reinterpret_cast<ET*>(smem + L.oF);
+    const ET* sD = reinterpret_cast<const ET*>(smem + L.oD);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.oT);
     const int KP = L.KP, gs = L.gs, dps = L.dps;
 
     // shared by every particle: F (uint16, row-major), D when it fits, the A tile
     // (row i < n holds F[i], rows up to `arows` are zero)
-    for (int i = tid; i < n * n; i += blockDim.x) sF[i] = (uint16_t)a.F[i];
+    for (int i = tid; i < n * n; i += blockDim.x) sF[i] = (ET)a.F[i];
     if (L.smem_d)
-        for (int i = tid; i < n * n; i += blockDim.x) const_cast<uint16_t*>(sD)[i] = (uint16_t)a.D[i];
+        for (int i = tid; i < n * n; i += blockDim.x) const_cast<ET*>(sD)[i] = (ET)a.D[i];
     for (int i = tid; i < L.arows * (KP / 8); i += blockDim.x) {
         const int r = i / (KP / 8), c = (i % (KP / 8)) * 8;
         uint32_t h[4];
@@ -658,14 +661,14 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
         *reinterpret_cast<uint4*>(sA + tc::tile_offset(r, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
     }
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(TEAMS * L.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)(TEAMS * L.groups * L.NP)) ncols <<= 1;
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
     if (tt == 0) mbar_init(bar, 1);
     fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tcol = *tslot + (uint32_t)(team * L.NP);
+    const uint32_t tcol = *tslot + (uint32_t)(team * L.groups * L.NP);
     const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
     const uint32_t sbo = (uint32_t)(KP / 8) * 128;
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
@@ -707,13 +710,24 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
                     if (c + q < n) v[q] = L.smem_d ? (int)sD[pm * n + pjq] : __ldg(a.D + pm * n + pjq);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
-                    const int j = c + 2 * q;
-                    if (j + 1 < n)
-                        *reinterpret_cast<uint32_t*>(Dp + m * dps + j) = (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
-                    else if (j < n)
-                        Dp[m * dps + j] = (uint16_t)v[2 * q];
+                for (int q = 0; q < 4; ++q) h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
+                if (c + 8 <= n) {  // whole words of Dp (rows start on 4 bytes)
+                    if (sizeof(ET) == 2) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            *reinterpret_cast<uint32_t*>(Dp + m * dps + c + 2 * q) =
+                                (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+                            *reinterpret_cast<uint32_t*>(Dp + m * dps + c + 4 * q) =
+                                (uint32_t)v[4 * q] | ((uint32_t)v[4 * q + 1] << 8) | ((uint32_t)v[4 * q + 2] << 16) |
+                                ((uint32_t)v[4 * q + 3] << 24);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (c + q < n) Dp[m * dps + c + q] = (ET)v[q];
                 }
             }
             *reinterpret_cast<uint4*>(U + tc::tile_offset(m, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -723,9 +737,10 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
         if (tt == 0) {
             tc::fence_after_sync();
             const uint32_t b0 = smem_u32(U);
-            for (int s = 0; s < KP / 16; ++s)
-                tc::mma_f16(tcol, tc::smem_desc(a_base + s * 256, 128, sbo), tc::smem_desc(b0 + s * 256, 128, sbo),
-                            idesc, s > 0);
+            for (int g = 0; g < L.groups; ++g)  // accumulator rows 128 g .. 128 g + 127
+                for (int s = 0; s < KP / 16; ++s)
+                    tc::mma_f16(tcol + (uint32_t)(g * L.NP), tc::smem_desc(a_base + g * 16 * sbo + s * 256, 128, sbo),
+                                tc::smem_desc(b0 + s * 256, 128, sbo), idesc, s > 0);
             tc::mma_commit(bar);
         }
         const bool ok = team_all<WPP>(mbar_wait(bar, phase), team);
@@ -738,18 +753,20 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
         // G_p from tensor memory (it overwrites the B tile, which the completed
         // product no longer reads): reader warp w holds rows k = 32 (w % WPP) + lane
         if (reader) {
-            const int k = 32 * (warp % WPP) + lane;
-            for (int c = 0; c < L.NP; c += 16) {
-                uint32_t v[16];
-                tc::tmem_ld16(tcol + ((uint32_t)(32 * wq) << 16) + (uint32_t)c, v);
-                tc::tmem_wait_ld();
-                if (k < n) {
+            for (int g = 0; g < L.groups; ++g) {
+                const int k = 128 * g + 32 * (warp % WPP) + lane;
+                for (int c = 0; c < L.NP; c += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tcol + (uint32_t)(g * L.NP) + ((uint32_t)(32 * wq) << 16) + (uint32_t)c, v);
+                    tc::tmem_wait_ld();
+                    if (k < n) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (c + q < n) H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q]));
+                        for (int q = 0; q < 16; ++q)
+                            if (c + q < n) H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q]));
+                    }
                 }
+                if (k < n) ev[k] = H[k * gs + k];  // G[k][p(k)]
             }
-            if (k < n) ev[k] = H[k * gs + k];  // G[k][p(k)]
         }
         tc::fence_before_sync();
         team_sync<WPP>(team);
@@ -759,7 +776,7 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
         if (ph < nph && col < n)
             for (int k = ph; k < n; k += nph) H[k * gs + col] -= ev[k];
         team_sync<WPP>(team);
-        descend_team<WPP>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
+        descend_team<WPP, ET>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
         team_sync<WPP>(team);
     }
     tc::fence_before_sync();
@@ -769,34 +786,34 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1) k_ls_t
 
 // CTAs of one launch that fit an SM: shared memory (all of the unified storage as
 // shared memory), threads, and the 512 tensor-memory columns
-template <int WPP>
-int team_ctas_per_sm(const TeamLayout<WPP>& T) {
+template <int WPP, typename ET>
+int team_ctas_per_sm(const TeamLayout<WPP, ET>& T) {
     int smem_sm = 0, reserved = 0;
     smem_limits(&smem_sm, &reserved);
     int c = smem_sm / (int)(T.total + reserved);
     const int threads = 32 * WPP * T.teams;
     const int by_threads = 2048 / threads;
     if (c > by_threads) c = by_threads;
-    const int regs = kernel_regs<k_ls_team<WPP>>();
+    const int regs = kernel_regs<k_ls_team<WPP, ET>>();
     if (regs > 0 && c > 65536 / (regs * threads)) c = 65536 / (regs * threads);
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(T.teams * T.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)(T.teams * T.groups * T.NP)) ncols <<= 1;
     if (c > (int)(512 / ncols)) c = (int)(512 / ncols);
     return c < 1 ? 1 : c;
 }
 
-template <int WPP>
+template <int WPP, typename ET>
 cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
     // D in shared memory when it fits, unless reading it through the cache lets
     // more CTAs share an SM
-    TeamLayout<WPP> T = team_layout<WPP>(L.n_max, true);
+    TeamLayout<WPP, ET> T = team_layout<WPP, ET>(L.n_max, true);
     if (T.smem_d) {
-        const TeamLayout<WPP> T2 = team_layout<WPP>(L.n_max, false);
+        const TeamLayout<WPP, ET> T2 = team_layout<WPP, ET>(L.n_max, false);
         if (team_ctas_per_sm(T2) > team_ctas_per_sm(T)) T = T2;
     }
     if (T.total > kSmemLimit) return cudaErrorInvalidValue;
     const int threads = 32 * WPP * T.teams;
-    cudaError_t e = configure_once<k_ls_team<WPP>>();
+    cudaError_t e = configure_once<k_ls_team<WPP, ET>>();
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     const int per_sm = team_ctas_per_sm(T);
@@ -809,7 +826,7 @@ cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
     }
     e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
     if (e != cudaSuccess) return e;
-    k_ls_team<WPP><<<L.count * cpi, threads, T.total, st>>>(L.d_args, cpi, T.smem_d ? 1 : 0);
+    k_ls_team<WPP, ET><<<L.count * cpi, threads, T.total, st>>>(L.d_args, cpi, T.smem_d ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -840,25 +857,32 @@ cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-int ls_max_n() {
-    int n = 2;
+int ls_max_n(int tc_flags) {
+    int n = 2;  // the SIMT kernel: one warp's G and the staged F, D in shared memory
     while (n < 256 && shared_part(n + 1) + warp_part(n + 1) <= kSmemLimit) ++n;
-    return n < 160 ? n : 160;
+    if (n > 160) n = 160;
+    if ((tc_flags & 3) == 3 && n < 160) n = 160;  // the 8-bit tensor-core search
+    return n;
 }
 
 LsKind ls_kind(const LsArgs& a) {
     const char* env = getenv("QAP_PSO_LS_SETUP");
     const bool simt = env && strcmp(env, "simt") == 0;
-    if (!a.tc_exact || a.n > 128 || simt) return LS_SIMT;
-    return a.n <= 32 ? LS_TEAM1 : (a.n <= 64 ? LS_TEAM2 : LS_TEAM8);
+    if (!(a.tc_exact & 1) || (simt && a.n <= ls_max_n(0))) return LS_SIMT;
+    if (a.n <= 32) return LS_TEAM1;
+    if (a.n <= 64) return LS_TEAM2;
+    if (a.n <= 128) return LS_TEAM8;
+    // past 128 rows only the 8-bit staging of F and Dp (entries <= 255) fits shared memory
+    return (a.tc_exact & 2) && a.n <= 160 ? LS_TEAM8N : LS_SIMT;
 }
 
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
     if (L.count <= 0 || L.total <= 0) return cudaSuccess;
-    if (L.n_max < 2 || L.n_max > ls_max_n()) return cudaErrorInvalidValue;
-    if (L.kind == LS_TEAM1) return launch_team<1>(L, st);
-    if (L.kind == LS_TEAM2) return launch_team<2>(L, st);
-    if (L.kind == LS_TEAM8) return launch_team<8>(L, st);
+    if (L.n_max < 2 || L.n_max > ls_max_n(L.kind == LS_TEAM8N ? 3 : 0)) return cudaErrorInvalidValue;
+    if (L.kind == LS_TEAM1) return launch_team<1, uint16_t>(L, st);
+    if (L.kind == LS_TEAM2) return launch_team<2, uint16_t>(L, st);
+    if (L.kind == LS_TEAM8) return launch_team<8, uint16_t>(L, st);
+    if (L.kind == LS_TEAM8N) return launch_team<8, uint8_t>(L, st);
     switch ((L.n_max + 31) / 32) {
         case 1: return launch_nw<1>(L, st);
         case 2: return launch_nw<2>(L, st);

@@ -28,14 +28,15 @@ struct LsArgs {
     int64_t* costL;
     unsigned long long* counters;  // may be null
     int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
-    int32_t tc_exact;  // symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
-                       // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT)
+    int32_t tc_exact;  // bit 0: symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
+                       // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT);
+                       // bit 1: also every entry <= 255 (8-bit staging of F and D)
     int32_t* work;     // device counter handing out this population's particles (zeroed
                        // by the launcher before every launch)
 };
 
 // Which local-search kernel serves a population, and the launch shape.
-enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_KINDS = 4 };
+enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_TEAM8N = 4, LS_KINDS = 5 };
 LsKind ls_kind(const LsArgs& a);
 
 // One local-search launch over `count` populations of the same kind.
@@ -49,7 +50,8 @@ struct LsLaunch {
     int total;             // particles over the table (automatic shape)
 };
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st);
-int ls_max_n();
+// largest n the local search serves (tc_flags: LsArgs::tc_exact of the instance)
+int ls_max_n(int tc_flags);
 
 // The velocity and position launches over `count` populations (flat index over
 // particles).

@@ -15,7 +15,7 @@ struct qap_instance {
     int32_t max_f, max_d;
     int32_t exact32;
     int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
-    int32_t tc_exact;   // the tensor-core set-up of the local search is exact
+    int32_t tc_exact;   // bit 0: the tensor-core set-up of the local search is exact; bit 1: and 8-bit staging fits
 };
 
 // One population. Its kernels read it through one-entry device tables (the same

@@ -28,6 +28,8 @@ INSTANCES = {
     "n100": lambda: W.dense_uniform(100, 7),
     "n128grid": lambda: W.grid_sparse(128, 8),
     "n150": lambda: W.dense_uniform(150, 9),
+    "n80wide": lambda: W.dense_uniform(80, 11, 0, 400),  # entries above 255: 16-bit staging
+    "n160grid": lambda: W.grid_sparse(160, 12),
 }
 
 
@@ -58,7 +60,7 @@ def test_eval_costs_general_instance(Q):
 def test_local_search_bit_exact(Q, name, cap):
     inst = INSTANCES[name]()
     gi = Q.Instance(inst.F, inst.D)
-    count = 40 if inst.n <= 64 else 9
+    count = 40 if inst.n <= 64 else 9  # the oracle's search is O(n^3) per round
     perms = W.random_perms(count, inst.n, 11)
     gp, gc, gm, gr = gi.local_search(perms, cap)
     for i, p in enumerate(perms):
@@ -132,7 +134,7 @@ def test_iterations_replay(Q, variant, name, m, ss):
         before = after
 
 
-@pytest.mark.parametrize("name", ["n2", "n3", "n65grid", "n100", "n150"])
+@pytest.mark.parametrize("name", ["n2", "n3", "n65grid", "n80wide", "n100", "n150", "n160grid"])
 def test_iterations_replay_edge_sizes(Q, name):
     inst = INSTANCES[name]()
     prm = Q.default_params(swarms=2, swarm_size=5, depth=min(2, inst.n - 1), mig_kind=1,
@@ -237,10 +239,13 @@ def test_invalid_params(Q):
 
 
 @pytest.mark.parametrize("setup", ["tc", "simt"])
-@pytest.mark.parametrize("name", ["n3", "tiny9", "dense30", "n33", "grid64", "n65grid", "n97", "n128grid"])
+@pytest.mark.parametrize("name", ["n3", "tiny9", "dense30", "n33", "grid64", "n65grid", "n97", "n128grid",
+                                  "n80wide", "n150", "n160grid"])
 def test_local_search_both_setups(Q, setup, name, monkeypatch):
     # the tensor-core and SIMT set-ups of G give identical searches
     if setup == "simt":
+        if name == "n160grid":
+            pytest.skip("n = 160 exceeds the SIMT search's shared memory; only the tensor-core search serves it")
         monkeypatch.setenv("QAP_PSO_LS_SETUP", "simt")
     else:
         monkeypatch.delenv("QAP_PSO_LS_SETUP", raising=False)

@@ -124,15 +124,19 @@ def aggregate(units, span_s, dist, torch, device):
 
 
 def algorithmic(n, dmoves, drounds, particles, swarms, storage_bytes):
-    """Work of one iteration (the per-unit figures of the design document's roofline
-    notes): velocity bytes (V read and written, X and P^L read, P^G once per swarm),
-    position bytes (V read, X read, S_x result written), local-search integer ops
-    (5 per swap value per round, 2 per entry of the rank-1 update per move) and the
-    set-up's tensor flops (2 n^3 per particle)."""
+    """Algorithmic work of one iteration: velocity bytes (V read and written, X and P^L
+    read, P^G once per swarm), position bytes (V read, X read, S_x result written),
+    local-search integer ops (below; dmoves = accepted moves in the iteration) and the
+    set-up product's tensor flops (2 n^3 per particle)."""
     npairs = n * (n - 1) // 2
     vel_bytes = particles * (2 * n * n * storage_bytes + 2 * n) + swarms * n
     pos_bytes = particles * (n * n * storage_bytes + 2 * n)
-    ls_ops = drounds * npairs * 5 + dmoves * 2 * n * n
+    # integer ops of the goal function and a swap local search with a Delta table
+    # (symmetric form): n(n-1)/2 for the cost, 3 (n-2) per pair for the table, and per
+    # accepted move 3 (n-2) per pair touching the swapped positions plus 7 per other pair
+    touching = 2 * (n - 2) + 1
+    ls_ops = (particles * (npairs + npairs * (n - 2) * 3)
+              + dmoves * (touching * (n - 2) * 3 + (npairs - touching) * 7))
     ls_tc_flops = particles * 2 * n ** 3
     return vel_bytes, pos_bytes, ls_ops, ls_tc_flops
 

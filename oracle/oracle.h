@@ -39,7 +39,8 @@ void orc_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t tag
 double orc_u01(uint32_t u);                  /* (u >> 8) * 2^-24, in [0, 1) */
 uint32_t orc_below(uint32_t u, uint32_t k);  /* floor(u * k / 2^32), in [0, k) */
 
-enum { ORC_TAG_R = 0, ORC_TAG_TIE = 1, ORC_TAG_INIT_X = 2, ORC_TAG_INIT_V = 3, ORC_TAG_MIG = 4 };
+enum { ORC_TAG_R = 0, ORC_TAG_TIE = 1, ORC_TAG_INIT_X = 2, ORC_TAG_INIT_V = 3, ORC_TAG_MIG = 4,
+       ORC_TAG_COLUMNS = 7 };
 
 /* ---- QAP goal function and swap neighbourhood (section 2.1) ---- */
 int64_t orc_cost(int n, const int32_t* F, const int32_t* D, const int32_t* p);
@@ -69,6 +70,7 @@ typedef struct {
     int32_t mig_period;
     int32_t ring_if_better;
     int32_t v_storage;      /* 0 = fp32, 1 = bf16 (round to nearest even) */
+    int32_t sx_kind;        /* 0 = SecondTarget (GlobalMax at depth 0), 1 = PickColumn */
 } orc_params;
 
 typedef struct {
@@ -104,6 +106,12 @@ void orc_velocity(const orc_params* q, int n, const double* V, const int32_t* x,
 int orc_second_target(const orc_params* q, int n, const float* Y, const int32_t* z,
                       uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, int32_t* out_p,
                       int32_t* order /* n x 2 picks (r, c) in order, may be NULL */);
+/* PickColumn(Y) (section 3.1): the columns in a random order (a Fisher-Yates
+ * shuffle, Philox tag 7, counter (c0, c1, c2)); each takes the largest element of
+ * its column over the rows still free. Returns the number of columns whose maximum
+ * was shared by several rows. order (may be NULL) receives the picks (r, c). */
+int orc_pick_column(const orc_params* q, int n, const float* Y, uint64_t seed, uint32_t c0, uint32_t c1,
+                    uint32_t c2, int32_t* out_p, int32_t* order);
 
 /* One particle's whole iteration (Eq. 4, Eq. 5, S_x, cost, local search), given
  * its state at the start of iteration t. V_new receives V(t+1). p_sx receives the

@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("depth", C.c_int32), ("sx_rule", C.c_int32), ("tie_rule", C.c_int32),
         ("pos_uses_new_v", C.c_int32), ("ls_max_moves", C.c_int32), ("ls_at_init", C.c_int32),
         ("mig_kind", C.c_int32), ("mig_depth", C.c_int32), ("mig_period", C.c_int32),
-        ("ring_if_better", C.c_int32), ("v_storage", C.c_int32),
+        ("ring_if_better", C.c_int32), ("v_storage", C.c_int32), ("sx_kind", C.c_int32),
     ]
 
 
@@ -100,6 +100,9 @@ def lib():
             L.orc_second_target.argtypes = [C.POINTER(Params), C.c_int, _F32P, _I32P, C.c_uint64,
                                             C.c_uint32, C.c_uint32, C.c_uint32, _I32P, C.c_void_p]
             L.orc_second_target.restype = C.c_int
+            L.orc_pick_column.argtypes = [C.POINTER(Params), C.c_int, _F32P, C.c_uint64, C.c_uint32,
+                                          C.c_uint32, C.c_uint32, _I32P, C.c_void_p]
+            L.orc_pick_column.restype = C.c_int
             L.orc_particle_iteration.argtypes = [
                 C.POINTER(Params), C.c_int, _I32P, _I32P, C.c_uint64, C.c_int, C.c_int, C.c_int,
                 _F64P, _I32P, _I32P, _I32P, _F64P, _I32P, _I32P, C.POINTER(C.c_int64),
@@ -118,7 +121,7 @@ def lib():
 
 DEFAULTS = dict(swarms=1, swarm_size=32, c1=0.8, c2=0.5, c3=0.5, sv_kind=1, v_max=1.0, depth=2,
                 sx_rule=0, tie_rule=0, pos_uses_new_v=0, ls_max_moves=0, ls_at_init=0,
-                mig_kind=0, mig_depth=0, mig_period=1, ring_if_better=0, v_storage=0)
+                mig_kind=0, mig_depth=0, mig_period=1, ring_if_better=0, v_storage=0, sx_kind=0)
 
 
 def make_params(**kw) -> Params:
@@ -213,6 +216,17 @@ def second_target(q: Params, Y, z, seed=0, c0=0, c1=0, c2=0, want_order=False):
     order = np.zeros((n, 2), np.int32)
     ties = lib().orc_second_target(C.byref(q), n, np.ascontiguousarray(Y, np.float32), _i32(z),
                                    seed, c0, c1, c2, out, order.ctypes.data if want_order else None)
+    if want_order:
+        return out, ties, order
+    return out, ties
+
+
+def pick_column(q: Params, Y, seed=0, c0=0, c1=0, c2=0, want_order=False):
+    n = Y.shape[0]
+    out = np.zeros(n, np.int32)
+    order = np.zeros((n, 2), np.int32)
+    ties = lib().orc_pick_column(C.byref(q), n, np.ascontiguousarray(Y, np.float32), seed, c0, c1, c2, out,
+                                 order.ctypes.data if want_order else None)
     if want_order:
         return out, ties, order
     return out, ties

@@ -67,6 +67,67 @@ void orc_velocity(const orc_params* q, int n, const double* V, const int32_t* x,
 
 /* ------------------------------------------------------------------- S_x */
 
+/* PickColumn(Y), section 3.1: "picks a column c, selects a maximum element x_rc,
+ * replaces it by 1 and clears other elements in r and c", until every column is
+ * assigned. The paper leaves the order of the columns open; here it is a
+ * Fisher-Yates shuffle of 0..n-1 (i = n-1 .. 1, j uniform in [0, i], draw q = n-1-i
+ * is word q mod 4 of block q/4 of tag 7 with counter (particle, swarm, t)), and the
+ * k-th column of the shuffled order is taken at step k. A maximum shared by several
+ * free rows is resolved like a tie of Algorithm 1: the rows in ascending order,
+ * element floor(u m / 2^32) with u = word (step mod 4) of block step/4 of tag 1
+ * (tie_rule 0), or the first (tie_rule 1). Comparisons on the fp32 values of Y. */
+int orc_pick_column(const orc_params* q, int n, const float* Y, uint64_t seed, uint32_t c0, uint32_t c1,
+                    uint32_t c2, int32_t* out_p, int32_t* order) {
+    int32_t* cols = (int32_t*)malloc(sizeof(int32_t) * n);
+    unsigned char* free_r = (unsigned char*)malloc(n);
+    int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * n);
+    for (int c = 0; c < n; ++c) cols[c] = c;
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (int i = n - 1; i >= 1; --i) {
+        const int d = n - 1 - i;
+        if (d % 4 == 0) orc_draw(seed, c0, c1, c2, ORC_TAG_COLUMNS, (uint32_t)(d / 4), w);
+        const int j = (int)orc_below(w[d % 4], (uint32_t)(i + 1));
+        const int32_t tmp = cols[i];
+        cols[i] = cols[j];
+        cols[j] = tmp;
+    }
+    memset(free_r, 1, n);
+    int ties = 0;
+    for (int step = 0; step < n; ++step) {
+        const int c = cols[step];
+        float best = 0.0f;
+        int m = 0;
+        for (int r = 0; r < n; ++r) {
+            if (!free_r[r]) continue;
+            const float y = Y[r * n + c];
+            if (m == 0 || y > best) {
+                best = y;
+                m = 0;
+            }
+            if (y == best) rows[m++] = r;
+        }
+        int k = 0;
+        if (m > 1) {
+            ++ties;
+            if (q->tie_rule == 0) {
+                orc_draw(seed, c0, c1, c2, ORC_TAG_TIE, (uint32_t)(step / 4), w);
+                k = (int)orc_below(w[step % 4], (uint32_t)m);
+            }
+        }
+        const int r = rows[k];
+        out_p[c] = r;
+        free_r[r] = 0;
+        if (order) {
+            order[2 * step] = r;
+            order[2 * step + 1] = c;
+        }
+    }
+    free(cols);
+    free(free_r);
+    free(rows);
+    return ties;
+}
+
 /* SecondTarget(Y, Z, depth), Algorithm 1: n greedy steps; each step takes the set
  * M of the largest remaining elements (rows and columns already used are gone),
  * picks one (r, c) of M, assigns facility c to location r and deletes row r and
@@ -183,8 +244,9 @@ void orc_particle_iteration(const orc_params* q, int n, const int32_t* F, const 
             float vv = (float)Vsrc[i * n + j];
             Y[i * n + j] = vv + xv;
         }
-    int nt = orc_second_target(q, n, Y, x, seed, (uint32_t)pis, (uint32_t)swarm, (uint32_t)t,
-                               p_sx, NULL);
+    int nt = q->sx_kind == 1
+                 ? orc_pick_column(q, n, Y, seed, (uint32_t)pis, (uint32_t)swarm, (uint32_t)t, p_sx, NULL)
+                 : orc_second_target(q, n, Y, x, seed, (uint32_t)pis, (uint32_t)swarm, (uint32_t)t, p_sx, NULL);
     free(Y);
     memcpy(p_out, p_sx, sizeof(int32_t) * n);
     int mv = 0;

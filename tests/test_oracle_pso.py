@@ -406,3 +406,70 @@ def test_step_bookkeeping_invariants():
         for k in range(3):
             assert O.cost(inst.F, inst.D, s.PG[k]) == s.costG[k]
         assert s.best_cost[0] <= hist_min.min()
+
+
+# ------------------------------------------------------------ PickColumn (section 3.1)
+
+def test_pick_column_is_a_greedy_over_columns():
+    # every pick is a largest element of its column among the rows still free
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 5, 9, 13):
+        for rep in range(6):
+            Y = rng.normal(size=(n, n)).astype(np.float32)
+            if rep % 2:
+                Y = np.round(Y * 2) / 2  # many equal values
+            q = O.make_params(sx_kind=1, tie_rule=rep % 2)
+            p, ties, order = O.pick_column(q, Y, seed=rep, c0=rep, want_order=True)
+            assert sorted(p) == list(range(n))
+            assert sorted(order[:, 1]) == list(range(n))  # every column once
+            free = np.ones(n, bool)
+            for r, c in order:
+                assert free[r] and Y[r, c] == Y[free, c].max()
+                free[r] = False
+            assert all(p[c] == r for r, c in order)
+
+
+def test_pick_column_distinct_column_maxima_is_argmax():
+    # maxima of the columns in distinct rows: the result is the column-wise argmax,
+    # whatever the order of the columns
+    rng = np.random.default_rng(12)
+    for n in (3, 8, 20):
+        perm = rng.permutation(n)
+        Y = (rng.random((n, n)) * 0.5).astype(np.float32)
+        Y[perm, np.arange(n)] += 1.0
+        for seed in range(5):
+            p, ties = O.pick_column(O.make_params(sx_kind=1), Y, seed=seed)
+            assert np.array_equal(p, perm) and ties == 0
+
+
+def test_pick_column_all_equal_first_rule():
+    # all values equal and the first element taken: the k-th column of the order gets
+    # the k-th row
+    n = 7
+    Y = np.zeros((n, n), np.float32)
+    p, ties, order = O.pick_column(O.make_params(sx_kind=1, tie_rule=1), Y, seed=3, want_order=True)
+    assert ties == n - 1
+    assert np.array_equal(order[:, 0], np.arange(n))
+
+
+def test_pick_column_order_uniform():
+    # the column order is a uniform permutation (Fisher-Yates from Philox)
+    n = 3
+    Y = np.eye(n, dtype=np.float32) * 0  # all equal, first rule: the order shows in the rows
+    counts = {}
+    for seed in range(1200):
+        _, _, order = O.pick_column(O.make_params(sx_kind=1, tie_rule=1), Y, seed=seed, want_order=True)
+        key = tuple(order[:, 1])
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 6
+    chi2 = sum((c - 200) ** 2 / 200 for c in counts.values())
+    assert chi2 < 20.5  # 5 degrees of freedom, p ~ 0.001
+
+
+def test_pick_column_random_ties_uniform():
+    n = 2
+    Y = np.zeros((n, n), np.float32)
+    first_rows = [O.pick_column(O.make_params(sx_kind=1), Y, seed=s, want_order=True)[2][0, 0]
+                  for s in range(800)]
+    frac = np.mean(first_rows)
+    assert 0.42 < frac < 0.58

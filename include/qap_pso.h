@@ -77,6 +77,7 @@ enum { PSO_SX_ALG1 = 0, PSO_SX_TOPD = 1 };             /* which elements SecondT
 enum { PSO_TIE_RANDOM = 0, PSO_TIE_FIRST = 1 };        /* choice inside the set M of Algorithm 1 */
 enum { PSO_MIG_NONE = 0, PSO_MIG_RANK = 1, PSO_MIG_RING = 2 };
 enum { PSO_V_FP32 = 0, PSO_V_BF16 = 1 };               /* storage of V; arithmetic is fp32 */
+enum { PSO_SXK_SECOND_TARGET = 0, PSO_SXK_PICK_COLUMN = 1 }; /* the S_x procedure (section 3.1) */
 
 typedef struct {
     int32_t swarms;         /* m >= 1 */
@@ -98,6 +99,10 @@ typedef struct {
     int32_t mig_period;     /* migrate after every mig_period-th iteration (>= 1) */
     int32_t ring_if_better; /* ring: replace P^G of swarm k+1 only if strictly better */
     int32_t v_storage;      /* PSO_V_FP32 or PSO_V_BF16 (round to nearest even) */
+    int32_t sx_kind;        /* PSO_SXK_SECOND_TARGET (Algorithm 1; GlobalMax at depth 0) or
+                               PSO_SXK_PICK_COLUMN: the columns in a random order (Philox
+                               Fisher-Yates, tag 7), each taking its largest element over the
+                               free rows; depth and sx_rule do not apply */
 } pso_params_t;
 
 /* Fills the defaults: m = 1, 32 particles, c1 = 0.8, c2 = c3 = 0.5 (the esc32
@@ -245,7 +250,7 @@ int qap_delta_table(qap_instance_t inst, const int32_t* perm, int64_t* out);
 /* Position discretisation alone (S_x = SecondTarget, Algorithm 1 of section 3.1)
  * of `count` matrices: Y (host, count x n x n fp32, row = location, column =
  * facility) and Z (host, count x n int32 permutations, facility -> location; the
- * ones of X(t)). The depth, sx_rule and tie_rule of `params` apply (its other
+ * ones of X(t)). The sx_kind, depth, sx_rule and tie_rule of `params` apply (its other
  * fields are ignored); random ties draw from the same Philox stream as an
  * iteration of particle particle[i] of swarm swarm[i] at iteration t (host arrays
  * of count int32). out_perm: host, count x n int32. This is the S_x of pso_step

@@ -37,7 +37,7 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     return U4{c0, c1, c2, c3};
 }
 
-enum : uint32_t { TAG_R = 0, TAG_TIE = 1, TAG_INIT_X = 2, TAG_INIT_V = 3, TAG_MIG = 4 };
+enum : uint32_t { TAG_R = 0, TAG_TIE = 1, TAG_INIT_X = 2, TAG_INIT_V = 3, TAG_MIG = 4, TAG_COLUMNS = 7 };
 
 __device__ __forceinline__ U4 draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                                     uint32_t tag, uint32_t block) {
@@ -164,7 +164,7 @@ struct StateView {
     unsigned long long* counters;
     uint64_t seed;
     float c1, c2, c3, v_max;
-    int32_t sv_kind, sx_rule, depth, tie_rule, pos_uses_new_v;
+    int32_t sv_kind, sx_rule, depth, tie_rule, pos_uses_new_v, sx_kind;
     int32_t ls_max_moves, mig_kind, mig_depth, mig_period, ring_if_better;
     // S_x alone (the discretisation entry point): V holds Y itself, X holds Z, and
     // the Philox counters of particle p are (sx_pis[p], sx_swarm[p], *t)

@@ -335,6 +335,11 @@ constexpr int kXchBytes = 256;  // per team: reduction slots and the next partic
 
 __host__ __device__ inline size_t round128(size_t x) { return (x + 127) & ~size_t(127); }
 
+template <typename ET>
+__host__ __device__ constexpr int team_groups() {
+    return sizeof(ET) == 1 ? 2 : 1;
+}
+
 // two integers (exact in fp16: |v| <= 2048) as a half2 word, a in the low half
 __device__ __forceinline__ uint32_t pack_h2(int a, int b) {
     return (uint32_t)__half_as_ushort(__int2half_rn(a)) | ((uint32_t)__half_as_ushort(__int2half_rn(b)) << 16);
@@ -351,10 +356,11 @@ __host__ __device__ inline TeamLayout<WPP, ET> team_layout(int n, bool allow_sme
     L.NP = L.KP;
     L.gs = n | 1;            // odd word stride: column accesses of H free of bank conflicts
     L.dps = L.KP + 4 / ES;   // odd word stride of the rows of Dp
-    // accumulator rows: one M = 128 product, two past 128 rows (A rows 128.. second)
-    L.groups = n > 128 ? 2 : 1;
+    // accumulator rows: one M = 128 product with 16-bit staging (n <= 128); the 8-bit
+    // variant serves 128 < n <= 160 with two (A rows 128.. in the second)
+    L.groups = team_groups<ET>();
     L.mrows = 128 * L.groups;
-    L.arows = WPP >= 4 ? (n > 128 ? L.KP : 128) : 32 * WPP;
+    L.arows = WPP >= 4 ? (L.groups == 2 ? L.KP : 128) : 32 * WPP;
     // team block: union(B tile, H), Dp, then the small arrays
     const size_t b_bytes = (size_t)L.NP * L.KP * 2, h_bytes = (size_t)n * L.gs * 4;
     L.tU = 0;
@@ -661,14 +667,14 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         *reinterpret_cast<uint4*>(sA + tc::tile_offset(r, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
     }
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(TEAMS * L.groups * L.NP)) ncols <<= 1;
+    while (ncols < (uint32_t)(TEAMS * team_groups<ET>() * L.NP)) ncols <<= 1;
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
     if (tt == 0) mbar_init(bar, 1);
     fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tcol = *tslot + (uint32_t)(team * L.groups * L.NP);
+    const uint32_t tcol = *tslot + (uint32_t)(team * team_groups<ET>() * L.NP);
     const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
     const uint32_t sbo = (uint32_t)(KP / 8) * 128;
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
@@ -737,7 +743,8 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         if (tt == 0) {
             tc::fence_after_sync();
             const uint32_t b0 = smem_u32(U);
-            for (int g = 0; g < L.groups; ++g)  // accumulator rows 128 g .. 128 g + 127
+#pragma unroll
+            for (int g = 0; g < team_groups<ET>(); ++g)  // accumulator rows 128 g .. 128 g + 127
                 for (int s = 0; s < KP / 16; ++s)
                     tc::mma_f16(tcol + (uint32_t)(g * L.NP), tc::smem_desc(a_base + g * 16 * sbo + s * 256, 128, sbo),
                                 tc::smem_desc(b0 + s * 256, 128, sbo), idesc, s > 0);
@@ -753,7 +760,8 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         // G_p from tensor memory (it overwrites the B tile, which the completed
         // product no longer reads): reader warp w holds rows k = 32 (w % WPP) + lane
         if (reader) {
-            for (int g = 0; g < L.groups; ++g) {
+#pragma unroll
+            for (int g = 0; g < team_groups<ET>(); ++g) {
                 const int k = 128 * g + 32 * (warp % WPP) + lane;
                 for (int c = 0; c < L.NP; c += 16) {
                     uint32_t v[16];

@@ -37,7 +37,8 @@ __host__ __device__ inline size_t tile_bytes(int n) {
 }
 template <typename VT>
 __host__ __device__ inline size_t warp_bytes(int n) {
-    return tile_bytes<VT>(n) + 96;  // + deleted-row bits (8 words) + the tail's row/column lists
+    // + deleted-row bits (8 words) + the tail's row/column lists or PickColumn's order
+    return tile_bytes<VT>(n) + 32 + align16((size_t)(n > 64 ? n : 64));
 }
 
 // --------------------------------------------------------------------- init
@@ -260,6 +261,94 @@ __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const
 #pragma unroll
         for (int sl = 0; sl < kTailSlots; ++sl)
             if ((rc[sl] >> 8) == ri || (rc[sl] & 0xFF) == ci) key[sl] = 0u;
+    }
+    return ties;
+}
+
+// PickColumn (section 3.1) on Y for one particle: the columns in a Fisher-Yates
+// order (Philox tag 7; lane 0 shuffles into shared memory), each taking its largest
+// element over the free rows; a maximum shared by several rows is resolved like a
+// tie of Algorithm 1 (rows ascending, element k of the tie draw, or the first).
+// Rows are spread over the lanes (row i = lane + 32 w). Returns the number of ties.
+template <int NW, typename VT>
+__device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, uint32_t* dead, uint8_t* order,
+                                           int n, int lane, const int (&pic)[NW], uint32_t pis, uint32_t swarm,
+                                           uint32_t t, float zadd, int (&newp)[NW]) {
+    if (lane == 0) {
+        for (int c = 0; c < n; ++c) order[c] = (uint8_t)c;
+        U4 u{0, 0, 0, 0};
+        for (int i = n - 1; i >= 1; --i) {
+            const int d = n - 1 - i;
+            if ((d & 3) == 0) u = draw(s.seed, pis, swarm, t, TAG_COLUMNS, (uint32_t)(d >> 2));
+            const int j = (int)below(word_of(u, d & 3), (uint32_t)(i + 1));
+            const uint8_t tmp = order[i];
+            order[i] = order[j];
+            order[j] = tmp;
+        }
+    }
+    if (lane < NW) dead[lane] = 0u;
+    __syncwarp();
+    int ties = 0;
+    for (int step = 0; step < n; ++step) {
+        const int c = order[step];
+        int pz = -1;  // the X(t) row of column c (held by lane c mod 32, slot c / 32)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int v = __shfl_sync(FULL, pic[w], c & 31);
+            if (w == (c >> 5)) pz = v;
+        }
+        uint32_t key[NW];
+        uint32_t lm = 0u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int i = lane + 32 * w;
+            key[w] = 0u;
+            if (i < n && !((dead[w] >> lane) & 1u)) {
+                float y = VStore<VT>::to_f(tile[i * n + c]);
+                if (i == pz) y += zadd;
+                key[w] = fkey(y);
+            }
+            lm = max(lm, key[w]);
+        }
+        const uint32_t gm = __reduce_max_sync(FULL, lm);
+        unsigned b[NW];
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            b[w] = __ballot_sync(FULL, key[w] != 0u && key[w] == gm);
+            tot += __popc(b[w]);
+        }
+        int kk = 0;
+        if (tot > 1) {
+            ++ties;
+            if (s.tie_rule == 0) {
+                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                kk = (int)below(word_of(u, step & 3), (uint32_t)tot);
+            }
+        }
+        int r = -1;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int cw = __popc(b[w]);
+            if (r < 0 && kk < cw) {
+                unsigned m = b[w];
+                for (int j = 0; j < kk; ++j) m &= m - 1u;  // drop the kk lower members
+                r = 32 * w + __ffs(m) - 1;
+            } else if (r < 0) {
+                kk -= cw;
+            }
+        }
+        if (r < 0 || r >= n) {  // cannot happen; never index with it
+            if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            return ties;
+        }
+        if (lane == (c & 31)) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (w == (c >> 5)) newp[w] = r;
+        }
+        if (lane == 0) dead[r >> 5] |= 1u << (r & 31);
+        __syncwarp();
     }
     return ties;
 }
@@ -907,8 +996,11 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
         // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
         // the discretisation entry point
-        const int ties =
-            second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, sx_only ? 0.0f : 1.0f, newp);
+        const float zadd = sx_only ? 0.0f : 1.0f;
+        const int ties = s.sx_kind == 1
+                             ? pick_column<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic,
+                                                   pis, swarm, t, zadd, newp)
+                             : second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, zadd, newp);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;

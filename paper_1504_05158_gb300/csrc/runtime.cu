@@ -46,13 +46,15 @@ int validate(const qap_instance* inst, const pso_params_t* p) {
     if (!(p->v_max > 0.0f)) return QAP_ERR_INVALID_ARG;
     if (p->sv_kind != PSO_SV_RAW && p->sv_kind != PSO_SV_NORM) return QAP_ERR_INVALID_ARG;
     if (p->sx_rule != PSO_SX_ALG1 && p->sx_rule != PSO_SX_TOPD) return QAP_ERR_INVALID_ARG;
-    if (p->depth < 0 || p->depth >= n) return QAP_ERR_INVALID_ARG;  // d < n (section 3.1)
+    if (p->sx_kind == PSO_SXK_SECOND_TARGET && (p->depth < 0 || p->depth >= n))
+        return QAP_ERR_INVALID_ARG;  // d < n (section 3.1); PickColumn has no depth
     if (p->tie_rule != PSO_TIE_RANDOM && p->tie_rule != PSO_TIE_FIRST) return QAP_ERR_INVALID_ARG;
     if (p->mig_kind < PSO_MIG_NONE || p->mig_kind > PSO_MIG_RING) return QAP_ERR_INVALID_ARG;
     if (p->mig_depth < 0 || 2 * p->mig_depth >= p->swarms + (p->mig_kind == PSO_MIG_RANK ? 0 : 1 << 30))
         return QAP_ERR_INVALID_ARG;  // d < m / 2 (Algorithm 2)
     if (p->mig_period < 1) return QAP_ERR_INVALID_ARG;
     if (p->v_storage != PSO_V_FP32 && p->v_storage != PSO_V_BF16) return QAP_ERR_INVALID_ARG;
+    if (p->sx_kind != PSO_SXK_SECOND_TARGET && p->sx_kind != PSO_SXK_PICK_COLUMN) return QAP_ERR_INVALID_ARG;
     if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
     if ((p->ls_max_moves >= 0) && !inst->sym_zd) return QAP_ERR_UNSUPPORTED;
     if (n > ls_max_n(inst->tc_exact) || n > velocity_sx_max_n(p->v_storage)) return QAP_ERR_UNSUPPORTED;
@@ -347,6 +349,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     sv.sx_rule = params->sx_rule;
     sv.depth = params->depth;
     sv.tie_rule = params->tie_rule;
+    sv.sx_kind = params->sx_kind;
     sv.pos_uses_new_v = params->pos_uses_new_v;
     sv.ls_max_moves = params->ls_max_moves;
     sv.mig_kind = params->mig_kind;
@@ -741,8 +744,10 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     if (!Y || !Z || !params || !swarm || !particle || !out_perm) return QAP_ERR_INVALID_ARG;
     if (n < 2 || n > 256 || count < 0 || t < 0) return QAP_ERR_INVALID_ARG;
     if (params->sx_rule != PSO_SX_ALG1 && params->sx_rule != PSO_SX_TOPD) return QAP_ERR_INVALID_ARG;
-    if (params->depth < 0 || params->depth >= n) return QAP_ERR_INVALID_ARG;
+    if (params->sx_kind == PSO_SXK_SECOND_TARGET && (params->depth < 0 || params->depth >= n))
+        return QAP_ERR_INVALID_ARG;  // d < n (section 3.1); PickColumn has no depth
     if (params->tie_rule != PSO_TIE_RANDOM && params->tie_rule != PSO_TIE_FIRST) return QAP_ERR_INVALID_ARG;
+    if (params->sx_kind != PSO_SXK_SECOND_TARGET && params->sx_kind != PSO_SXK_PICK_COLUMN) return QAP_ERR_INVALID_ARG;
     if (n > velocity_sx_max_n(0)) return QAP_ERR_UNSUPPORTED;
     if (count == 0) return QAP_OK;
     for (int i = 0; i < count; ++i) {
@@ -793,6 +798,7 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     sv.sx_rule = params->sx_rule;
     sv.depth = params->depth;
     sv.tie_rule = params->tie_rule;
+    sv.sx_kind = params->sx_kind;
     sv.sx_only = 1;
     sv.sx_swarm = (const int32_t*)(base + oSw);
     sv.sx_pis = (const int32_t*)(base + oPi);

@@ -20,6 +20,7 @@ SX_ALG1, SX_TOPD = 0, 1
 TIE_RANDOM, TIE_FIRST = 0, 1
 MIG_NONE, MIG_RANK, MIG_RING = 0, 1, 2
 V_FP32, V_BF16 = 0, 1
+SXK_SECOND_TARGET, SXK_PICK_COLUMN = 0, 1
 
 # every exported symbol of include/qap_pso.h
 EXPORTS = [
@@ -47,7 +48,7 @@ class Params(C.Structure):
         ("sx_rule", C.c_int32), ("depth", C.c_int32), ("tie_rule", C.c_int32),
         ("pos_uses_new_v", C.c_int32), ("ls_max_moves", C.c_int32), ("ls_at_init", C.c_int32),
         ("mig_kind", C.c_int32), ("mig_depth", C.c_int32), ("mig_period", C.c_int32),
-        ("ring_if_better", C.c_int32), ("v_storage", C.c_int32),
+        ("ring_if_better", C.c_int32), ("v_storage", C.c_int32), ("sx_kind", C.c_int32),
     ]
 
     def as_dict(self):

@@ -79,7 +79,10 @@ def compare_step(q, F, D, seed, before, after, prm, sample=None):
             # S_x on the device's own V(t+1): decisions on identical fp32 inputs
             Y = (after["V"][p].astype(np.float32) + (np.arange(n)[:, None] == before["X"][p][None, :]))
             Y = Y.astype(np.float32)
-            psx, _ = O.second_target(q, Y, before["X"][p], seed, i, k, t)
+            if q.sx_kind == 1:
+                psx, _ = O.pick_column(q, Y, seed, i, k, t)
+            else:
+                psx, _ = O.second_target(q, Y, before["X"][p], seed, i, k, t)
             assert np.array_equal(psx, after["X_sx"][p]), f"S_x differs at particle {p}"
             pls, c, mv, _, _ = O.local_search(F, D, psx, q.ls_max_moves) if q.ls_max_moves >= 0 \
                 else (psx, O.cost(F, D, psx), 0, 0, None)

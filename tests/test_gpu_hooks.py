@@ -111,3 +111,28 @@ def test_discretize_rejects_bad_input(Q):
     with pytest.raises(Q.QapError):
         Q.discretize(np.zeros((1, 4, 4), np.float32), np.arange(4, dtype=np.int32),
                      Q.default_params(depth=4), 1, 0, 0, 0)  # depth >= n
+
+
+@pytest.mark.parametrize("n", [2, 3, 9, 33, 64, 100, 150])
+@pytest.mark.parametrize("tie", [0, 1])
+@pytest.mark.parametrize("quantised", [False, True])
+def test_discretize_pick_column_matches_oracle(Q, n, tie, quantised):
+    count = 12
+    Y, Z = _ys(count, n, 300 + n, quantised)
+    seed = 0xC0FFEE + n
+    swarm = np.arange(count, dtype=np.int32) % 4
+    particle = np.arange(count, dtype=np.int32) * 3
+    t = 5
+    g = Q.default_params(sx_kind=1, tie_rule=tie)
+    q = O.make_params(sx_kind=1, tie_rule=tie)
+    got = Q.discretize(Y, Z, g, seed, swarm, particle, t)
+    for i in range(count):
+        want, _ = O.pick_column(q, Y[i], seed, int(particle[i]), int(swarm[i]), t)
+        assert np.array_equal(got[i], want), i
+
+
+def test_invalid_sx_kind(Q):
+    with pytest.raises(Q.QapError) as e:
+        Q.discretize(np.zeros((1, 4, 4), np.float32), np.arange(4, dtype=np.int32), Q.default_params(sx_kind=2),
+                     1, 0, 0, 0)
+    assert e.value.status == Q.ERR_INVALID_ARG

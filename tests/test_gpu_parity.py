@@ -113,6 +113,8 @@ VARIANTS = {
     "rank": dict(mig_kind=1, mig_depth=1, mig_period=1),
     "ring": dict(mig_kind=2, mig_period=2),
     "ringbetter": dict(mig_kind=2, mig_period=1, ring_if_better=1),
+    "pickcol": dict(sx_kind=1),
+    "pickcol_newv_first": dict(sx_kind=1, pos_uses_new_v=1, tie_rule=1),
 }
 
 

@@ -171,6 +171,18 @@ typedef struct {
 /* Population statistics of the current costs plus counters (synchronises). */
 int pso_stats(pso_state_t st, pso_stats_t* out);
 
+/* The same statistics over the particles of one swarm (0 <= swarm < m): the
+ * percentile ranks the paper plots for its most successful swarms (section 4.2);
+ * the counters are those of the whole population. Synchronous. */
+int pso_stats_swarm(pso_state_t st, int32_t swarm, pso_stats_t* out);
+
+/* Distribution of the current costs (the probability mass function of section 4.2,
+ * up to the factor 1 / particles) of one swarm, or of every particle (swarm = -1):
+ * counts (host, bins + 2 int64) receives [0] the costs below lo, [1 + b] those with
+ * floor((cost - lo) bins / (hi - lo)) = b, [bins + 1] those at or above hi.
+ * 1 <= bins <= 2^20, lo < hi. Synchronous. Errors: QAP_ERR_INVALID_ARG. */
+int pso_cost_histogram(pso_state_t st, int32_t swarm, int64_t lo, int64_t hi, int32_t bins, int64_t* counts);
+
 void pso_destroy(pso_state_t st);
 
 /* ------------------------------------------------ state export / import */

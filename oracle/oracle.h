@@ -131,6 +131,9 @@ void orc_step(const orc_params* q, int n, const int32_t* F, const int32_t* D, ui
 void orc_bests_and_migration(const orc_params* q, int n, uint64_t seed, int t, orc_state* s);
 
 /* Nearest-rank percentiles of P costs: out = {min, p5, p25, p50, p75, max}, *mean. */
+/* Histogram of costs: counts[0] below lo, counts[1 + b] for b = floor((cost - lo) bins /
+ * (hi - lo)), counts[bins + 1] at or above hi (the PMF of section 4.2 times P). */
+void orc_histogram(const int64_t* cost, int P, int64_t lo, int64_t hi, int bins, int64_t* counts);
 void orc_stats(const int64_t* cost, int P, int64_t out[6], double* mean);
 
 #ifdef __cplusplus

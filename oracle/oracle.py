@@ -113,6 +113,8 @@ def lib():
             L.orc_bests_and_migration.argtypes = [C.POINTER(Params), C.c_int, C.c_uint64, C.c_int,
                                                   C.POINTER(_State)]
             L.orc_stats.argtypes = [_I64P, C.c_int, _I64P, C.POINTER(C.c_double)]
+            L.orc_histogram.argtypes = [_I64P, C.c_int, C.c_int64, C.c_int64, C.c_int, _I64P]
+            L.orc_histogram.restype = None
             _lib = L
     return _lib
 
@@ -306,6 +308,13 @@ def bests_and_migration(q: Params, seed, t, s: State) -> State:
     cs = s._c()
     lib().orc_bests_and_migration(C.byref(q), s.n, seed, t, C.byref(cs))
     return s
+
+
+def histogram(cost, lo, hi, bins):
+    cost = np.ascontiguousarray(cost, np.int64)
+    out = np.zeros(bins + 2, np.int64)
+    lib().orc_histogram(cost, len(cost), int(lo), int(hi), int(bins), out)
+    return out
 
 
 def stats(cost):

@@ -436,6 +436,27 @@ static int cmp_i64(const void* a, const void* b) {
 
 /* Percentile ranks of the goal values of a population (section 4.2): nearest
  * rank, P_q = sorted[ceil(q N) - 1]. */
+void orc_histogram(const int64_t* cost, int P, int64_t lo, int64_t hi, int bins, int64_t* counts) {
+    for (int b = 0; b < bins + 2; ++b) counts[b] = 0;
+    for (int i = 0; i < P; ++i) {
+        if (cost[i] < lo) {
+            counts[0] += 1;
+        } else if (cost[i] >= hi) {
+            counts[bins + 1] += 1;
+        } else {
+            /* the bin whose half-open interval [lo + b w, lo + (b + 1) w), w = (hi - lo) / bins,
+               holds the cost, found by scanning the bins in order */
+            for (int b = 0; b < bins; ++b) {
+                /* cost < lo + (b + 1)(hi - lo) / bins  <=>  (cost - lo) bins < (b + 1)(hi - lo) */
+                if ((__int128)(cost[i] - lo) * bins < (__int128)(b + 1) * (hi - lo)) {
+                    counts[1 + b] += 1;
+                    break;
+                }
+            }
+        }
+    }
+}
+
 void orc_stats(const int64_t* cost, int P, int64_t out[6], double* mean) {
     int64_t* v = (int64_t*)malloc(sizeof(int64_t) * P);
     memcpy(v, cost, sizeof(int64_t) * P);

@@ -6,6 +6,7 @@
 //   + sum_{k != r, s} (F_kr - F_ks)(D_{p_k p_s} - D_{p_k p_r})
 //                   + (F_rk - F_sk)(D_{p_s p_k} - D_{p_r p_k}),
 // accumulated in int64. One thread per pair; F and D are read through the cache.
+// Also the histogram of costs (the probability mass function of section 4.2).
 #include "kernels.h"
 
 namespace qap {
@@ -29,7 +30,34 @@ __global__ void k_delta_table(const int32_t* __restrict__ F, const int32_t* __re
     out[idx] = d;
 }
 
+// Costs binned by b = floor((cost - lo) bins / (hi - lo)) (exact 128-bit integer
+// arithmetic); counts[0]: below lo, counts[1 + b], counts[bins + 1]: at or above hi.
+__global__ void k_histogram(const int64_t* __restrict__ cost, int count, int64_t lo, int64_t hi, int bins,
+                            unsigned long long* __restrict__ counts) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const int64_t c = cost[i];
+        int slot;
+        if (c < lo) {
+            slot = 0;
+        } else if (c >= hi) {
+            slot = bins + 1;
+        } else {
+            const unsigned __int128 num = (unsigned __int128)(uint64_t)(c - lo) * (uint64_t)bins;
+            slot = 1 + (int)(num / (unsigned __int128)(uint64_t)(hi - lo));
+        }
+        atomicAdd(counts + slot, 1ull);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_histogram(const int64_t* cost, int count, int64_t lo, int64_t hi, int bins,
+                             unsigned long long* counts, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int grid = (count + 255) / 256 < 1024 ? (count + 255) / 256 : 1024;
+    k_histogram<<<grid, 256, 0, st>>>(cost, count, lo, hi, bins, counts);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_delta_table(const int32_t* F, const int32_t* D, int n, const int32_t* perm, int64_t* out,
                                cudaStream_t st) {

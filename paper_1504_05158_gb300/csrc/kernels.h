@@ -85,6 +85,11 @@ int bests_max_swarms();
 cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, int32_t scratch_len,
                          int64_t* out6, double* mean, cudaStream_t st);
 
+// Histogram of `count` device costs: counts (device, bins + 2, zeroed by the caller)
+// [0] below lo, [1 + b] for b = floor((cost - lo) bins / (hi - lo)), [bins + 1] >= hi.
+cudaError_t launch_histogram(const int64_t* cost, int count, int64_t lo, int64_t hi, int bins,
+                             unsigned long long* counts, cudaStream_t st);
+
 // Delta(r, s) of every pair r < s of one permutation (device pointers; out holds
 // n (n - 1) / 2 int64 in r-major pair order).
 cudaError_t launch_delta_table(const int32_t* F, const int32_t* D, int n, const int32_t* perm, int64_t* out,

@@ -454,9 +454,8 @@ int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
     return QAP_OK;
 }
 
-int pso_stats(pso_state_t s, pso_stats_t* out) {
-    if (!s || !out || out->size < sizeof(pso_stats_t)) return QAP_ERR_INVALID_ARG;
-    cudaError_t e = launch_stats(s->sv.cost, s->sv.P, s->stats_buf, s->stats_len, s->stats_out,
+static int stats_of_range(pso_state_t s, int32_t first, int32_t count, pso_stats_t* out) {
+    cudaError_t e = launch_stats(s->sv.cost + first, count, s->stats_buf, s->stats_len, s->stats_out,
                                  (double*)(s->stats_out + 6), s->stream);
     int64_t o[7];
     unsigned long long cnt[CNT_N];
@@ -485,6 +484,31 @@ int pso_stats(pso_state_t s, pso_stats_t* out) {
     out->sx_ties = (int64_t)cnt[CNT_TIES];
     out->errors = (int64_t)cnt[CNT_ERR];
     return QAP_OK;
+}
+
+int pso_stats(pso_state_t s, pso_stats_t* out) {
+    if (!s || !out || out->size < sizeof(pso_stats_t)) return QAP_ERR_INVALID_ARG;
+    return stats_of_range(s, 0, s->sv.P, out);
+}
+
+int pso_stats_swarm(pso_state_t s, int32_t swarm, pso_stats_t* out) {
+    if (!s || !out || out->size < sizeof(pso_stats_t) || swarm < 0 || swarm >= s->sv.m) return QAP_ERR_INVALID_ARG;
+    return stats_of_range(s, swarm * s->sv.ss, s->sv.ss, out);
+}
+
+int pso_cost_histogram(pso_state_t s, int32_t swarm, int64_t lo, int64_t hi, int32_t bins, int64_t* counts) {
+    if (!s || !counts || bins < 1 || bins > (1 << 20) || hi <= lo || swarm < -1 || swarm >= s->sv.m)
+        return QAP_ERR_INVALID_ARG;
+    const int first = swarm < 0 ? 0 : swarm * s->sv.ss, count = swarm < 0 ? s->sv.P : s->sv.ss;
+    unsigned long long* d = nullptr;
+    const size_t bytes = sizeof(unsigned long long) * (size_t)(bins + 2);
+    cudaError_t e = cudaMallocAsync(&d, bytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, bytes, s->stream);
+    if (e == cudaSuccess) e = launch_histogram(s->sv.cost + first, count, lo, hi, bins, d, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (d) cudaFreeAsync(d, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return status_of(e);
 }
 
 void pso_destroy(pso_state_t s) {

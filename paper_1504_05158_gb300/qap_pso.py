@@ -29,7 +29,7 @@ EXPORTS = [
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
     "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
     "pso_batch_size", "pso_batch_member", "pso_batch_destroy", "pso_footprint", "pso_poll",
-    "qap_delta_table", "pso_discretize",
+    "qap_delta_table", "pso_discretize", "pso_stats_swarm", "pso_cost_histogram",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -125,6 +125,8 @@ def lib():
         L.pso_footprint.argtypes = [C.c_int32, C.POINTER(Params), C.POINTER(C.c_size_t)]
         L.pso_poll.argtypes = [vp, C.POINTER(C.c_int32)]
         L.qap_delta_table.argtypes = [vp, vp, vp]
+        L.pso_stats_swarm.argtypes = [vp, C.c_int32, C.POINTER(Stats)]
+        L.pso_cost_histogram.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.c_int32, vp]
         L.pso_discretize.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(Params), C.c_uint64, vp, vp,
                                      C.c_int32, vp]
         _lib = L
@@ -292,6 +294,19 @@ class Swarm:
         s.size = C.sizeof(Stats)
         _check(lib().pso_stats(self.h, C.byref(s)), "pso_stats")
         return s.as_dict()
+
+    def stats_swarm(self, swarm):
+        """Statistics of one swarm's current costs (section 4.2's swarm percentiles)."""
+        s = Stats()
+        s.size = C.sizeof(Stats)
+        _check(lib().pso_stats_swarm(self.h, swarm, C.byref(s)), "pso_stats_swarm")
+        return s.as_dict()
+
+    def cost_histogram(self, lo, hi, bins, swarm=-1):
+        """Counts of current costs: [below lo, bins equal-width bins of [lo, hi), >= hi]."""
+        out = np.zeros(bins + 2, np.int64)
+        _check(lib().pso_cost_histogram(self.h, swarm, lo, hi, bins, _ptr(out)), "pso_cost_histogram")
+        return out
 
     def export_state(self):
         n, P, m = self.n, self.P, self.params.swarms

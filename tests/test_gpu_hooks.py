@@ -136,3 +136,27 @@ def test_invalid_sx_kind(Q):
         Q.discretize(np.zeros((1, 4, 4), np.float32), np.arange(4, dtype=np.int32), Q.default_params(sx_kind=2),
                      1, 0, 0, 0)
     assert e.value.status == Q.ERR_INVALID_ARG
+
+
+def test_swarm_stats_and_histogram(Q):
+    inst = W.grid64()
+    gi = Q.Instance(inst.F, inst.D)
+    sw = Q.Swarm(gi, Q.default_params(swarms=5, swarm_size=37, mig_kind=2, mig_period=3), seed=8)
+    for it in range(4):
+        sw.step(1)
+        st = sw.export_state()
+        cost = st["cost"]
+        for k in (0, 2, 4):
+            got = sw.stats_swarm(k)
+            want = O.stats(cost[k * 37:(k + 1) * 37])
+            keys = ("min", "p5", "p25", "p50", "p75", "max")
+            assert [got[x] for x in keys] == [want[x] for x in keys]
+            assert abs(got["mean"] - want["mean"]) <= 1e-9 * abs(want["mean"])
+        lo, hi = int(cost.min()) + 17, int(cost.max()) - 5
+        for bins, swarm in ((1, -1), (7, -1), (50, 3)):
+            sel = cost if swarm < 0 else cost[swarm * 37:(swarm + 1) * 37]
+            assert np.array_equal(sw.cost_histogram(lo, hi, bins, swarm), O.histogram(sel, lo, hi, bins))
+    with pytest.raises(Q.QapError):
+        sw.stats_swarm(5)
+    with pytest.raises(Q.QapError):
+        sw.cost_histogram(10, 10, 4)

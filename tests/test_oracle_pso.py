@@ -473,3 +473,29 @@ def test_pick_column_random_ties_uniform():
                   for s in range(800)]
     frac = np.mean(first_rows)
     assert 0.42 < frac < 0.58
+
+
+def test_histogram_by_brute_force():
+    # the bins against exact rational edges computed with Python integers
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        P = int(rng.integers(1, 200))
+        cost = rng.integers(-50, 1000, P).astype(np.int64)
+        lo = int(rng.integers(-60, 300))
+        hi = lo + int(rng.integers(1, 900))
+        bins = int(rng.integers(1, 40))
+        got = O.histogram(cost, lo, hi, bins)
+        want = np.zeros(bins + 2, np.int64)
+        for c in cost.tolist():
+            if c < lo:
+                want[0] += 1
+            elif c >= hi:
+                want[-1] += 1
+            else:
+                w = Fraction(hi - lo, bins)
+                b = 0
+                while not (lo + b * w <= c < lo + (b + 1) * w):
+                    b += 1
+                want[1 + b] += 1
+        assert np.array_equal(got, want) and got.sum() == P

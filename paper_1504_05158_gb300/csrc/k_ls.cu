@@ -863,6 +863,392 @@ cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ general instances (any F, D)
+// The same search for F and D that need not be symmetric nor have a zero diagonal
+// (entries <= 2048, 2 n max_f max_d < 2^24; n <= 128). With Dp[k][m] = D[p(k)][p(m)],
+// R = F Dp^T and C = F^T Dp (R[a][m] = sum_j F[a][j] D[p(m)][p(j)], C[a][m] = sum_i
+// F[i][a] D[p(i)][p(m)]), the team keeps H[a][m] = (R + C)[a][m] - (R + C)[a][a];
+// then f(p) = trace(R + C) / 2 and
+//     delta(r, s) = H[r][s] + H[s][r] + K(r, s),
+// K collecting the terms of the general swap formula whose indices are only r and s.
+// A swap changes R and C by rank-1 terms (fR[k] = F[k][r] - F[k][s] against
+// eR[x] = Dp[x][s] - Dp[x][r]; fC[k] = F[r][k] - F[s][k] against eC[x] = Dp[s][x] -
+// Dp[r][x]); rows and columns r, s exchange with their own corrections, and Dp
+// exchanges rows and columns r and s. The set-up accumulates F Dp^T and F^T Dp in one
+// tensor-memory accumulator (two chains of tcgen05.mma, A = F and F^T shared by the
+// CTA, B = Dp and Dp^T per particle). One 8-warp team per CTA.
+struct GenLayout {
+    int n, KP, NP, gs, dps;
+    bool smem_d;
+    size_t oA1, oA2, oF, oD, oU, oDp, oPi, oRow, oCol, oEv, oX, oBar, oT, total;
+};
+
+__host__ __device__ inline GenLayout gen_layout(int n, bool allow_smem_d = true) {
+    GenLayout L{};
+    L.n = n;
+    L.KP = round_up(n, 16);
+    L.NP = L.KP;
+    L.gs = n | 1;
+    L.dps = L.KP + 2;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        const size_t r = o;
+        o = round128(o + b);
+        return r;
+    };
+    const size_t a_bytes = (size_t)128 * L.KP * 2, b_bytes = (size_t)L.NP * L.KP * 2;
+    const size_t h_bytes = (size_t)n * L.gs * 4;
+    L.oA1 = take(a_bytes);
+    L.oA2 = take(a_bytes);
+    L.oF = take((size_t)n * n * 2);
+    L.oU = take(2 * b_bytes > h_bytes ? 2 * b_bytes : h_bytes);  // B tiles, then H
+    L.oDp = take((size_t)n * L.dps * 2);
+    L.oPi = take(L.KP);
+    L.oRow = take((size_t)n * 16);
+    L.oCol = take((size_t)n * 8);
+    L.oEv = take((size_t)n * 4);
+    L.oX = take(kXchBytes);
+    L.oBar = take(8);
+    L.oT = take(16);
+    L.oD = o;
+    L.smem_d = allow_smem_d && o + round128((size_t)n * n * 2) <= kSmemLimit;
+    if (L.smem_d) o = round128(o + (size_t)n * n * 2);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void descend_gen(const LsArgs& a, int p, const uint16_t* sF, int32_t* H, uint16_t* Dp,
+                                            uint8_t* pi8, int4* rowv, int2* colv, int* xch, long long cost,
+                                            int gs, int dps, int tt) {
+    constexpr int TT = 256;
+    const int n = a.n;
+    const int lane = tt & 31, wi = tt >> 5;
+    const int slotw = round_up(n, 32) < TT ? round_up(n, 32) : TT;
+    const int nph = TT / slotw, ph = tt / slotw, e = tt % slotw;
+    const bool on = ph < nph && e < n;
+    const long long npairs = (long long)n * (n - 1) / 2;
+    const int nv = n / 2;
+    auto Fv = [&](int i, int j) { return (int)sF[i * n + j]; };
+    auto Dv = [&](int i, int j) { return (int)Dp[i * dps + j]; };
+    int moves = 0, rounds = 0;
+    if (a.max_moves >= 0) {
+        for (;;) {
+            if (a.max_moves > 0 && moves >= a.max_moves) break;
+            if (moves >= kSafetyMoves) {
+                if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            long long b0 = LLONG_MAX, b1 = LLONG_MAX;
+            if (on) {
+                auto pair_value = [&](int t) -> long long {
+                    const bool c1 = e < n - 1 - t;
+                    const int k = c1 ? t : n - 2 - t;
+                    const int m = c1 ? t + 1 + e : e;
+                    const int Fkk = Fv(k, k), Fmm = Fv(m, m), Fkm = Fv(k, m), Fmk = Fv(m, k);
+                    const int Dkk = Dv(k, k), Dmm = Dv(m, m), Dkm = Dv(k, m), Dmk = Dv(m, k);
+                    // the terms of the general formula with indices in {k, m} only
+                    const int corner = (Fkk - Fmm) * (Dmm - Dkk) + (Fkm - Fmk) * (Dmk - Dkm);
+                    const int sub = (Fkk - Fmk) * (Dmk - Dkk) + (Fkm - Fmm) * (Dmm - Dkm) +
+                                    (Fkk - Fkm) * (Dkm - Dkk) + (Fmk - Fmm) * (Dmm - Dmk);
+                    const int d = H[k * gs + m] + H[m * gs + k] + corner - sub;
+                    const long long v = (long long)d * 65536 + ((k << 8) | m);
+                    return (c1 || k != t) ? v : LLONG_MAX;
+                };
+                int t = ph;
+                for (; t + nph < nv; t += 2 * nph) {
+                    const long long v0 = pair_value(t), v1 = pair_value(t + nph);
+                    b0 = v0 < b0 ? v0 : b0;
+                    b1 = v1 < b1 ? v1 : b1;
+                }
+                for (; t < nv; t += nph) {
+                    const long long v0 = pair_value(t);
+                    b0 = v0 < b0 ? v0 : b0;
+                }
+            }
+            const long long bv = b1 < b0 ? b1 : b0;
+            int best = bv == LLONG_MAX ? INT_MAX : (int)(bv >> 16);
+            unsigned bkey = bv == LLONG_MAX ? 0xFFFFFFFFu : (unsigned)(bv & 0xFFFF);
+            team_min2<8>(best, bkey, xch, rounds & 1, 0, lane, wi);
+            ++rounds;
+            if (best >= 0) break;
+            const int r = (int)(bkey >> 8), s = (int)(bkey & 255u);
+            if (r >= n || s >= n || r >= s) {  // cannot happen; never index with it
+                if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            // A: the move's vectors and the old rows and columns r, s of H and Dp
+            const int hrs = H[r * gs + s], hsr = H[s * gs + r];
+            const int fRr = Fv(r, r) - Fv(r, s), fRs = Fv(s, r) - Fv(s, s);
+            const int fCr = Fv(r, r) - Fv(s, r), fCs = Fv(r, s) - Fv(s, s);
+            const int eRr = Dv(r, s) - Dv(r, r), eRs = Dv(s, s) - Dv(s, r);
+            const int eCr = Dv(s, r) - Dv(r, r), eCs = Dv(s, s) - Dv(r, s);
+            const int drr = Dv(r, r), dss = Dv(s, s), drs = Dv(r, s), dsr = Dv(s, r);
+            const int x = tt;
+            int fR = 0, fC = 0, eR = 0, eC = 0, hxr = 0, hxs = 0, hrx = 0, hsx = 0;
+            int dxr = 0, dxs = 0, drx = 0, dsx = 0;
+            if (x < n) {
+                fR = Fv(x, r) - Fv(x, s);
+                fC = Fv(r, x) - Fv(s, x);
+                dxr = Dv(x, r);
+                dxs = Dv(x, s);
+                drx = Dv(r, x);
+                dsx = Dv(s, x);
+                eR = dxs - dxr;
+                eC = dsx - drx;
+                hxr = H[x * gs + r];
+                hxs = H[x * gs + s];
+                hrx = H[r * gs + x];
+                hsx = H[s * gs + x];
+                const bool rs = x == r || x == s;
+                rowv[x] = make_int4(rs ? 0 : fR, rs ? 0 : fC, fR * eR + fC * eC, 0);
+                colv[x] = make_int2(eR, eC);
+            }
+            team_sync<8>(0);
+            // B: rows and columns outside {r, s}
+            if (on && e != r && e != s) {
+                const int2 ce = colv[e];
+                for (int k = ph; k < n; k += nph) {
+                    const int4 q = rowv[k];
+                    if (q.x | q.y) H[k * gs + e] += q.x * ce.x + q.y * ce.y - q.z;
+                }
+            }
+            // C: rows and columns r and s
+            if (x < n && x != r && x != s) {
+                H[x * gs + r] = hxs + fR * (eRs - eR) + fC * (eCs - eC);
+                H[x * gs + s] = hxr + fR * (eRr - eR) + fC * (eCr - eC);
+                H[r * gs + x] = hrx - hrs + fRr * (eR - eRs) + fCr * (eC - eCs);
+                H[s * gs + x] = hsx - hsr + fRs * (eR - eRr) + fCs * (eC - eCr);
+                Dp[x * dps + r] = (uint16_t)dxs;
+                Dp[x * dps + s] = (uint16_t)dxr;
+                Dp[r * dps + x] = (uint16_t)dsx;
+                Dp[s * dps + x] = (uint16_t)drx;
+            }
+            if (tt == 0) {
+                H[r * gs + s] = -hrs + fRr * (eRr - eRs) + fCr * (eCr - eCs);
+                H[s * gs + r] = -hsr + fRs * (eRs - eRr) + fCs * (eCs - eCr);
+                Dp[r * dps + r] = (uint16_t)dss;
+                Dp[s * dps + s] = (uint16_t)drr;
+                Dp[r * dps + s] = (uint16_t)dsr;
+                Dp[s * dps + r] = (uint16_t)drs;
+                const uint8_t t8 = pi8[r];
+                pi8[r] = pi8[s];
+                pi8[s] = t8;
+            }
+            team_sync<8>(0);
+            cost += best;
+            ++moves;
+        }
+    }
+    for (int m = tt; m < n; m += TT) a.out[(size_t)p * a.ps_out + m] = pi8[m];
+    if (a.PL) {
+        const long long old = a.costL[p];
+        if (cost < old) {
+            for (int m = tt; m < n; m += TT) a.PL[(size_t)p * a.ps_out + m] = pi8[m];
+            if (tt == 0) a.costL[p] = cost;
+        }
+    }
+    if (tt == 0) {
+        a.cost[p] = cost;
+        if (a.moves) a.moves[p] = moves;
+        if (a.rounds) a.rounds[p] = rounds;
+        if (a.counters) {
+            atomicAdd(a.counters + CNT_PIT, 1ull);
+            if (a.max_moves >= 0) {
+                atomicAdd(a.counters + CNT_MOVES, (unsigned long long)moves);
+                atomicAdd(a.counters + CNT_ROUNDS, (unsigned long long)rounds);
+                if (rounds > 0) {
+                    atomicAdd(a.counters + CNT_DELTA_FULL, (unsigned long long)npairs);
+                    atomicAdd(a.counters + CNT_DELTA_INCR, (unsigned long long)((rounds - 1) * npairs));
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_ls_gen(const LsArgs* __restrict__ args, int cpi, int smem_d) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const LsArgs a = args[blockIdx.x / cpi];
+    const int cb = blockIdx.x % cpi;
+    const int n = a.n;
+    const GenLayout L = gen_layout(n, smem_d != 0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sA1 = smem + L.oA1;
+    unsigned char* sA2 = smem + L.oA2;
+    uint16_t* sF = reinterpret_cast<uint16_t*>(smem + L.oF);
+    const uint16_t* sD = reinterpret_cast<const uint16_t*>(smem + L.oD);
+    unsigned char* U = smem + L.oU;
+    unsigned char* B2 = U + (size_t)L.NP * L.KP * 2;
+    int32_t* H = reinterpret_cast<int32_t*>(U);
+    uint16_t* Dp = reinterpret_cast<uint16_t*>(smem + L.oDp);
+    uint8_t* pi8 = smem + L.oPi;
+    int4* rowv = reinterpret_cast<int4*>(smem + L.oRow);
+    int2* colv = reinterpret_cast<int2*>(smem + L.oCol);
+    int32_t* ev = reinterpret_cast<int32_t*>(smem + L.oEv);
+    int* xch = reinterpret_cast<int*>(smem + L.oX);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.oBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.oT);
+    const int KP = L.KP, gs = L.gs, dps = L.dps;
+
+    for (int i = tid; i < n * n; i += blockDim.x) sF[i] = (uint16_t)a.F[i];
+    if (L.smem_d)
+        for (int i = tid; i < n * n; i += blockDim.x) const_cast<uint16_t*>(sD)[i] = (uint16_t)a.D[i];
+    // A1 = F, A2 = F^T (rows >= n zero)
+    for (int i = tid; i < 128 * (KP / 8); i += blockDim.x) {
+        const int r = i / (KP / 8), c = (i % (KP / 8)) * 8;
+        uint32_t h1[4], h2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = c + 2 * q;
+            const bool r_in = r < n;
+            h1[q] = pack_h2(r_in && j < n ? a.F[r * n + j] : 0, r_in && j + 1 < n ? a.F[r * n + j + 1] : 0);
+            h2[q] = pack_h2(r_in && j < n ? a.F[j * n + r] : 0, r_in && j + 1 < n ? a.F[(j + 1) * n + r] : 0);
+        }
+        *reinterpret_cast<uint4*>(sA1 + tc::tile_offset(r, c, KP)) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+        *reinterpret_cast<uint4*>(sA2 + tc::tile_offset(r, c, KP)) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+    }
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)L.NP) ncols <<= 1;
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    if (tid == 0) mbar_init(bar, 1);
+    fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tcol = *tslot;
+    const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
+    const uint32_t sbo = (uint32_t)(KP / 8) * 128;
+    const int slotw = round_up(n, 32) < 256 ? round_up(n, 32) : 256;
+    const int nph = 256 / slotw, ph = tid / slotw, col = tid % slotw;
+    uint32_t phase = 0;
+    int next = cb;
+
+    for (;;) {
+        int p;
+        if (a.work) {
+            if (tid == 0) xch[60] = atomicAdd(a.work, 1);
+            team_sync<8>(0);
+            p = xch[60];
+            team_sync<8>(0);
+        } else {
+            p = next;
+            next += cpi;
+        }
+        if (p >= a.count) break;
+        for (int m = tid; m < KP; m += 256) pi8[m] = m < n ? a.in[(size_t)p * a.ps_in + m] : 0;
+        team_sync<8>(0);
+        // Dp (uint16 rows) and the B tiles Dp and Dp^T (fp16, zero padded)
+        for (int i = tid; i < L.NP * (KP / 8); i += 256) {
+            const int m = i / (KP / 8), c = (i % (KP / 8)) * 8;
+            uint32_t h1[4] = {0u, 0u, 0u, 0u}, h2[4] = {0u, 0u, 0u, 0u};
+            if (m < n) {
+                const int pm = pi8[m];
+                int v1[8], v2[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = c + q;
+                    v1[q] = 0;
+                    v2[q] = 0;
+                    if (j < n) {
+                        const int pj = pi8[j];
+                        v1[q] = L.smem_d ? (int)sD[pm * n + pj] : __ldg(a.D + pm * n + pj);  // Dp[m][j]
+                        v2[q] = L.smem_d ? (int)sD[pj * n + pm] : __ldg(a.D + pj * n + pm);  // Dp[j][m]
+                        Dp[m * dps + j] = (uint16_t)v1[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h1[q] = pack_h2(v1[2 * q], v1[2 * q + 1]);
+                    h2[q] = pack_h2(v2[2 * q], v2[2 * q + 1]);
+                }
+            }
+            *reinterpret_cast<uint4*>(U + tc::tile_offset(m, c, KP)) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+            *reinterpret_cast<uint4*>(B2 + tc::tile_offset(m, c, KP)) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+        }
+        fence_proxy_async();
+        team_sync<8>(0);
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2), b1 = smem_u32(U), b2 = smem_u32(B2);
+            for (int s = 0; s < KP / 16; ++s)  // F Dp^T
+                tc::mma_f16(tcol, tc::smem_desc(a1 + s * 256, 128, sbo), tc::smem_desc(b1 + s * 256, 128, sbo), idesc,
+                            s > 0);
+            for (int s = 0; s < KP / 16; ++s)  // + F^T Dp
+                tc::mma_f16(tcol, tc::smem_desc(a2 + s * 256, 128, sbo), tc::smem_desc(b2 + s * 256, 128, sbo), idesc,
+                            true);
+            tc::mma_commit(bar);
+        }
+        const bool ok = team_all<8>(mbar_wait(bar, phase), 0);
+        phase ^= 1u;
+        if (!ok) {
+            if (tid == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+            break;
+        }
+        tc::fence_after_sync();
+        if (warp < 4) {  // rows k = 32 warp + lane, lane quarter = warp
+            const int k = 32 * warp + lane;
+            for (int c = 0; c < L.NP; c += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(tcol + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+                tc::tmem_wait_ld();
+                if (k < n) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (c + q < n) H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q]));
+                }
+            }
+            if (k < n) ev[k] = H[k * gs + k];
+        }
+        tc::fence_before_sync();
+        team_sync<8>(0);
+        long long part = 0;
+        for (int m = tid; m < n; m += 256) part += ev[m];
+        const long long cost2 = team_sum64<8>(part, reinterpret_cast<long long*>(xch) + 16, 0, lane, tid >> 5);
+        if (ph < nph && col < n)
+            for (int k = ph; k < n; k += nph) H[k * gs + col] -= ev[k];
+        team_sync<8>(0);
+        descend_gen(a, p, sF, H, Dp, pi8, rowv, colv, xch, cost2 / 2, gs, dps, tid);
+        team_sync<8>(0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(*tslot, ncols);
+}
+
+cudaError_t launch_gen(const LsLaunch& L, cudaStream_t st) {
+    GenLayout T = gen_layout(L.n_max, true);
+    int smem_sm = 0, reserved = 0;
+    smem_limits(&smem_sm, &reserved);
+    auto ctas = [&](const GenLayout& G) {
+        int c = smem_sm / (int)(G.total + reserved);
+        const int regs = kernel_regs<k_ls_gen>();
+        if (regs > 0 && c > 65536 / (regs * 256)) c = 65536 / (regs * 256);
+        if (c > 8) c = 8;
+        uint32_t ncols = 32;
+        while (ncols < (uint32_t)G.NP) ncols <<= 1;
+        if (c > (int)(512 / ncols)) c = (int)(512 / ncols);
+        return c < 1 ? 1 : c;
+    };
+    if (T.smem_d) {
+        const GenLayout T2 = gen_layout(L.n_max, false);
+        if (ctas(T2) > ctas(T)) T = T2;
+    }
+    if (T.total > kSmemLimit) return cudaErrorInvalidValue;
+    cudaError_t e = configure_once<k_ls_gen>();
+    if (e != cudaSuccess) return e;
+    const int per_sm = ctas(T);
+    int cpi = L.cpi;
+    if (cpi <= 0) {
+        cpi = (sm_count() * per_sm + L.count - 1) / L.count;
+        const int per_pop = L.total / L.count;
+        if (cpi > per_pop) cpi = per_pop;
+        if (cpi < 1) cpi = 1;
+    }
+    e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
+    if (e != cudaSuccess) return e;
+    k_ls_gen<<<L.count * cpi, 256, T.total, st>>>(L.d_args, cpi, T.smem_d ? 1 : 0);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int ls_max_n(int tc_flags) {
@@ -876,7 +1262,8 @@ int ls_max_n(int tc_flags) {
 LsKind ls_kind(const LsArgs& a) {
     const char* env = getenv("QAP_PSO_LS_SETUP");
     const bool simt = env && strcmp(env, "simt") == 0;
-    if (!(a.tc_exact & 1) || (simt && a.n <= ls_max_n(0))) return LS_SIMT;
+    if (!(a.tc_exact & 1)) return (a.tc_exact & 4) && a.n <= 128 ? LS_GEN : LS_SIMT;
+    if (simt && a.n <= ls_max_n(0)) return LS_SIMT;
     if (a.n <= 32) return LS_TEAM1;
     if (a.n <= 64) return LS_TEAM2;
     if (a.n <= 128) return LS_TEAM8;
@@ -891,6 +1278,7 @@ cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
     if (L.kind == LS_TEAM2) return launch_team<2, uint16_t>(L, st);
     if (L.kind == LS_TEAM8) return launch_team<8, uint16_t>(L, st);
     if (L.kind == LS_TEAM8N) return launch_team<8, uint8_t>(L, st);
+    if (L.kind == LS_GEN) return launch_gen(L, st);
     switch ((L.n_max + 31) / 32) {
         case 1: return launch_nw<1>(L, st);
         case 2: return launch_nw<2>(L, st);

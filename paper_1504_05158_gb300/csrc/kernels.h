@@ -30,13 +30,16 @@ struct LsArgs {
     int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
     int32_t tc_exact;  // bit 0: symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
                        // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT);
-                       // bit 1: also every entry <= 255 (8-bit staging of F and D)
+                       // bit 1: also every entry <= 255 (8-bit staging of F and D);
+                       // bit 2: any F, D (not symmetric or not zero-diagonal) with entries
+                       // <= 2048, 2 n max_f max_d < 2^24 and n <= 128: the general
+                       // tensor-core search is exact
     int32_t* work;     // device counter handing out this population's particles (zeroed
                        // by the launcher before every launch)
 };
 
 // Which local-search kernel serves a population, and the launch shape.
-enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_TEAM8N = 4, LS_KINDS = 5 };
+enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_TEAM8N = 4, LS_GEN = 5, LS_KINDS = 6 };
 LsKind ls_kind(const LsArgs& a);
 
 // One local-search launch over `count` populations of the same kind.

@@ -56,7 +56,7 @@ int validate(const qap_instance* inst, const pso_params_t* p) {
     if (p->v_storage != PSO_V_FP32 && p->v_storage != PSO_V_BF16) return QAP_ERR_INVALID_ARG;
     if (p->sx_kind != PSO_SXK_SECOND_TARGET && p->sx_kind != PSO_SXK_PICK_COLUMN) return QAP_ERR_INVALID_ARG;
     if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
-    if ((p->ls_max_moves >= 0) && !inst->sym_zd) return QAP_ERR_UNSUPPORTED;
+    if ((p->ls_max_moves >= 0) && !inst->sym_zd && !(inst->tc_exact & 4)) return QAP_ERR_UNSUPPORTED;
     if (n > ls_max_n(inst->tc_exact) || n > velocity_sx_max_n(p->v_storage)) return QAP_ERR_UNSUPPORTED;
     return QAP_OK;
 }
@@ -203,6 +203,8 @@ int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_insta
     q->narrow_ok = md <= 65535 ? 1 : 0;
     q->tc_exact = (sym && mf <= 2048 && md <= 2048 && (long double)n * mf * md < (long double)(1 << 24)) ? 1 : 0;
     if (q->tc_exact && mf <= 255 && md <= 255) q->tc_exact |= 2;
+    if (!sym && n <= 128 && mf <= 2048 && md <= 2048 && 2.0L * n * mf * md < (long double)(1 << 24))
+        q->tc_exact |= 4;  // the general search
     const size_t bytes = (size_t)n * n * 4;
     cudaError_t e = cudaMalloc(&q->dF, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&q->dD, bytes);
@@ -733,7 +735,7 @@ int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t
     if (!inst || !perms || count < 0 || max_moves < 0) return QAP_ERR_INVALID_ARG;
     if (count == 0) return QAP_OK;
     if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
-    if (!inst->sym_zd) return QAP_ERR_UNSUPPORTED;
+    if (!inst->sym_zd && !(inst->tc_exact & 4)) return QAP_ERR_UNSUPPORTED;
     if (inst->n > ls_max_n(inst->tc_exact)) return QAP_ERR_UNSUPPORTED;
     return run_ls_hook(inst, perms, count, max_moves, perms, costs, moves, rounds);
 }

@@ -73,8 +73,8 @@ def test_local_search_rejects_bad_input(Q):
     gi = Q.Instance(inst.F, inst.D)
     with pytest.raises(Q.QapError):
         gi.local_search(np.zeros((1, 8), np.int32))  # not a permutation
-    asym = W.random_asymmetric(8, 2)
-    ga = Q.Instance(asym.F, asym.D)
+    big = W.random_asymmetric(8, 2, hi=3000)  # general instance beyond the exact fp16 set-up
+    ga = Q.Instance(big.F, big.D)
     with pytest.raises(Q.QapError) as e:
         ga.local_search(W.random_perms(1, 8, 1))
     assert e.value.status == Q.ERR_UNSUPPORTED
@@ -277,3 +277,57 @@ def test_large_values_use_exact_simt_setup(Q):
     for i, p in enumerate(perms):
         op, oc, om, orr, _ = O.local_search(F, D, p, 0)
         assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om, i
+
+
+# ------------------------------------------------------------ general instances
+
+def _diag_instance(n, seed):
+    """Symmetric F and D with a nonzero diagonal (installation costs)."""
+    inst = W.dense_uniform(n, seed, 0, 60)
+    rng = np.random.default_rng(seed)
+    F = inst.F.copy()
+    D = inst.D.copy()
+    F[np.arange(n), np.arange(n)] = rng.integers(0, 30, n)
+    D[np.arange(n), np.arange(n)] = rng.integers(0, 30, n)
+    return F, D
+
+
+@pytest.mark.parametrize("n,seed,hi", [(2, 1, 20), (3, 2, 20), (9, 3, 50), (21, 4, 200), (40, 5, 99),
+                                       (64, 6, 99), (97, 7, 60), (128, 8, 40)])
+@pytest.mark.parametrize("cap", [0, 2])
+def test_general_local_search_bit_exact(Q, n, seed, hi, cap):
+    inst = W.random_asymmetric(n, seed, hi=hi)
+    gi = Q.Instance(inst.F, inst.D)
+    assert gi.info()["symmetric_zero_diag"] == 0
+    perms = W.random_perms(12 if n <= 64 else 5, n, seed)
+    gp, gc, gm, gr = gi.local_search(perms, cap)
+    for i, p in enumerate(perms):
+        op, oc, om, orr, _ = O.local_search(inst.F, inst.D, p, cap)
+        assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om and gr[i] == orr, i
+    assert np.array_equal(gi.eval_costs(perms), [O.cost(inst.F, inst.D, p) for p in perms])
+
+
+def test_general_local_search_with_diagonal(Q):
+    F, D = _diag_instance(30, 9)
+    gi = Q.Instance(F, D)
+    perms = W.random_perms(16, 30, 9)
+    gp, gc, gm, gr = gi.local_search(perms, 0)
+    for i, p in enumerate(perms):
+        op, oc, om, orr, _ = O.local_search(F, D, p, 0)
+        assert np.array_equal(gp[i], op) and gc[i] == oc and gm[i] == om and gr[i] == orr, i
+
+
+@pytest.mark.parametrize("variant", ["default", "rank"])
+def test_general_iterations_replay(Q, variant):
+    inst = W.random_asymmetric(21, 4, hi=200)
+    kw = dict(swarms=3, swarm_size=9)
+    kw.update(VARIANTS[variant])
+    prm = Q.default_params(**kw)
+    sw = Q.Swarm(Q.Instance(inst.F, inst.D), prm, seed=77)
+    q = oracle_params(prm)
+    before = sw.export_state()
+    for _ in range(3):
+        sw.step(1)
+        after = sw.export_state()
+        compare_step(q, inst.F, inst.D, 77, before, after, prm)
+        before = after

@@ -364,11 +364,15 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     r = oracle_sample(steps=args.steps, warmup=args.warmup, budget_s=120.0)
+    cfg = workload_config("fp64 (oracle)")
+    cfg["l2"] = "host cores (no GPU)"
+    cfg["timing"] = ("wall clock of each step over a sample of the workload: 2 swarms x 32 particles "
+                     "of the same instance and parameters, scaled to particle-iterations/s")
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * 64 / r["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config("fp64 (oracle)"), "impl": "reference",
+            "config": cfg, "impl": "reference",
             "cpu_baseline": {k: r[k] for k in ("kind", "cores", "sample", "value", "unit")},
             "delta_evals_per_s": r["delta_evals_per_s"],
             "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -118,8 +118,9 @@ typedef struct pso_state* pso_state_t;
  * [-v_max, v_max), both from Philox; cost, P^L = X(0), P^G and the global best.
  * `stream` is a cudaStream_t (NULL = a new stream owned by the state). The state
  * keeps a pointer to `inst`, which must outlive it. Errors: QAP_ERR_INVALID_ARG
- * (bad parameters), QAP_ERR_UNSUPPORTED (local search requested on an instance
- * that is not symmetric with zero diagonal, or n above the device limit),
+ * (bad parameters), QAP_ERR_UNSUPPORTED (local search requested on a general
+ * instance — not symmetric, or with a nonzero diagonal — whose entries exceed 2048,
+ * 2 n max_f max_d >= 2^24 or n > 128; or n above the device limit),
  * QAP_ERR_OVERFLOW (values too large for the exact int32 path), QAP_ERR_OOM,
  * QAP_ERR_CUDA. */
 int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, void* stream,
@@ -246,8 +247,9 @@ int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int
 /* Best-improvement swap local search (the search of every iteration) on `count`
  * permutations (host, count x n int32, improved in place), max_moves as
  * pso_params_t.ls_max_moves (>= 0). Outputs (host, count entries each, any may be
- * NULL): final costs, moves, rounds (neighbourhood evaluations). Requires a
- * symmetric zero-diagonal instance. */
+ * NULL): final costs, moves, rounds (neighbourhood evaluations). General instances
+ * (not symmetric, or with a nonzero diagonal) need entries <= 2048,
+ * 2 n max_f max_d < 2^24 and n <= 128 (else QAP_ERR_UNSUPPORTED). */
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds);
 

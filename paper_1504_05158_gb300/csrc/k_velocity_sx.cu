@@ -35,10 +35,18 @@ template <typename VT>
 __host__ __device__ inline size_t tile_bytes(int n) {
     return align16((size_t)n * n * sizeof(VT));
 }
+// The row masks of the column caches of SecondTarget: word wi of column slot w of a
+// lane at em[(w nwr + wi) 32 + lane], nwr = the row words of the largest n served.
+__host__ __device__ inline size_t mask_bytes(int n) {
+    const size_t w = (size_t)(n + 31) / 32;
+    return w * w * 32 * sizeof(uint32_t);
+}
+__host__ __device__ inline size_t lists_bytes(int n) { return align16((size_t)(n > 64 ? n : 64)); }
 template <typename VT>
 __host__ __device__ inline size_t warp_bytes(int n) {
     // + deleted-row bits (8 words) + the tail's row/column lists or PickColumn's order
-    return tile_bytes<VT>(n) + 32 + align16((size_t)(n > 64 ? n : 64));
+    // + the row masks
+    return tile_bytes<VT>(n) + 32 + lists_bytes(n) + mask_bytes(n);
 }
 
 // --------------------------------------------------------------------- init
@@ -90,25 +98,28 @@ __global__ void k_init(StateView s) {
 
 // --------------------------------------------------------- velocity and S_x
 // Per-column cache of the largest plain velocity value V[i][c] over the remaining
-// rows i other than the column's X(t) row pz: value, multiplicity, first row. The
-// X(t) cell itself, Y[pz][c] = V[pz][c] + 1, is kept apart, so ignoring it (the
-// first `depth` steps) or losing it (row pz assigned) never forces a rescan. A
-// cache whose copies of the maximum have all been deleted keeps its value as an
-// upper bound (count 0) and is rescanned only when needed; +inf means never
-// scanned, -inf means no rows left. Deleted rows are bits of `dead` (shared memory,
-// one word per 32 rows). The scan reads 32 rows at a time with independent loads.
+// rows i other than the column's X(t) row pz: the value, its multiplicity and the
+// rows holding it (a bit mask over the rows, in shared memory). The X(t) cell itself,
+// Y[pz][c] = V[pz][c] + 1, is kept apart, so ignoring it (the first `depth` steps) or
+// losing it (row pz assigned) never forces a rescan. A deleted row leaves every
+// mask, so a cache whose rows have all gone keeps its value as an upper bound
+// (count 0) and is rescanned only when needed; +inf means never scanned, -inf means
+// no rows left. Deleted rows are bits of `dead` (shared memory, one word per 32
+// rows). The scan reads 32 rows at a time with independent loads.
 struct ColMax {
     float v;
-    int cnt, first;
+    int cnt;
 };
 
+// The maximum of column c over the remaining rows other than pz; em (the column's
+// mask, words 32 apart) receives the rows holding it.
 template <typename VT>
-__device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz) {
+__device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz, uint32_t* em) {
     const float kNegInf = __int_as_float(0xff800000);
-    ColMax r{kNegInf, 0, -1};
-    for (int base = 0; base < n; base += 32) {
-        uint32_t ok = ~dead[base >> 5];
-        if ((pz >> 5) == (base >> 5)) ok &= ~(1u << (pz & 31));
+    ColMax r{kNegInf, 0};
+    for (int base = 0, wi = 0; base < n; base += 32, ++wi) {
+        uint32_t ok = ~dead[wi];
+        if ((pz >> 5) == wi) ok &= ~(1u << (pz & 31));
         const int lim = n - base;
         if (lim < 32) ok &= (1u << lim) - 1u;
         float v[32];
@@ -121,44 +132,21 @@ __device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n
         uint32_t eq = 0u;
 #pragma unroll
         for (int b = 0; b < 32; ++b) eq |= (((ok >> b) & 1u) && v[b] == mx) ? (1u << b) : 0u;
+        uint32_t keep = 0u;
         if (eq) {
             if (r.cnt == 0 || mx > r.v) {
+                for (int k = 0; k < wi; ++k) em[32 * k] = 0u;  // a larger maximum: earlier rows leave
                 r.v = mx;
                 r.cnt = __popc(eq);
-                r.first = base + __ffs(eq) - 1;
+                keep = eq;
             } else if (mx == r.v) {
                 r.cnt += __popc(eq);
+                keep = eq;
             }
         }
+        em[32 * wi] = keep;
     }
     return r;
-}
-
-// first remaining row after r (other than pz) holding value vm in column c, or -1
-template <typename VT>
-__device__ __noinline__ int vnext(const VT* tile, const uint32_t* dead, int n, int c, int pz, float vm,
-                                  int r) {
-    for (int i = r + 1; i < n; ++i)
-        if (!((dead[i >> 5] >> (i & 31)) & 1u) && i != pz && VStore<VT>::to_f(tile[i * n + c]) == vm)
-            return i;
-    return -1;
-}
-
-// the kk-th remaining row (ascending) of column c whose Y value equals e, where the
-// X(t) row pz counts with value zv when the X(t) cell takes part (zin)
-template <typename VT>
-__device__ __noinline__ int kth_row(const VT* tile, const uint32_t* dead, int n, int c, int pz, bool zin,
-                                    float zv, float e, int kk) {
-    int seen = 0;
-    for (int i = 0; i < n; ++i) {
-        if ((dead[i >> 5] >> (i & 31)) & 1u) continue;
-        const bool hit = (i == pz) ? (zin && zv == e) : (VStore<VT>::to_f(tile[i * n + c]) == e);
-        if (hit) {
-            if (seen == kk) return i;
-            ++seen;
-        }
-    }
-    return -1;
 }
 
 // The last steps of SecondTarget once at most kTailCols columns are left and the
@@ -173,7 +161,7 @@ template <int NW, typename VT>
 __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const uint32_t* dead, uint8_t* lists,
                                        int n, int lane, const int (&pic)[NW], const bool (&alive)[NW],
                                        uint32_t pis, uint32_t swarm, uint32_t t, float zadd, int step, int A,
-                                       int (&newp)[NW]) {
+                                       U4& tu, int& tblk, int (&newp)[NW]) {
     uint8_t* rows = lists;       // remaining rows, ascending
     uint8_t* cols = lists + 16;  // remaining columns, ascending
     uint8_t* xrow = lists + 32;  // their X(t) rows
@@ -232,8 +220,11 @@ __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const
         if (tot > 1) {
             ++ties;
             if (s.tie_rule == 0) {
-                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
-                kk = (int)below(word_of(u, step & 3), (uint32_t)tot);
+                if ((step >> 2) != tblk) {  // one block of draws serves four steps
+                    tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                    tblk = step >> 2;
+                }
+                kk = (int)below(word_of(tu, step & 3), (uint32_t)tot);
             }
         }
         // the kk-th cell of M in cell order (slot, then lane)
@@ -289,6 +280,8 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
     if (lane < NW) dead[lane] = 0u;
     __syncwarp();
     int ties = 0;
+    U4 tu{0, 0, 0, 0};
+    int tblk = -1;
     for (int step = 0; step < n; ++step) {
         const int c = order[step];
         int pz = -1;  // the X(t) row of column c (held by lane c mod 32, slot c / 32)
@@ -322,8 +315,11 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
         if (tot > 1) {
             ++ties;
             if (s.tie_rule == 0) {
-                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
-                kk = (int)below(word_of(u, step & 3), (uint32_t)tot);
+                if ((step >> 2) != tblk) {
+                    tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                    tblk = step >> 2;
+                }
+                kk = (int)below(word_of(tu, step & 3), (uint32_t)tot);
             }
         }
         int r = -1;
@@ -365,14 +361,16 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
 // one round; equal values among them only reorder those steps (each group of g
 // equal values is g - 1 steps with a choice). Other steps run one at a time.
 template <int NW, typename VT>
-__device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, int n,
-                                             int lane, const int (&pic)[NW], uint32_t pis,
+__device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, uint32_t* em,
+                                             int nwr, int n, int lane, const int (&pic)[NW], uint32_t pis,
                                              uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW]) {
     const int depth = s.depth;
     if (lane < NW) dead[lane] = 0u;
     __syncwarp();
+    // word wi of column slot w's row mask
+    auto emw = [&](int w, int wi) -> uint32_t& { return em[(w * nwr + wi) * 32 + lane]; };
     float zv[NW], vm[NW];
-    int vc[NW], va[NW];
+    int vc[NW];
     bool alive[NW], zal[NW], ex[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -383,7 +381,6 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         zv[w] = alive[w] ? VStore<VT>::to_f(tile[pic[w] * n + c]) + zadd : 0.0f;
         vm[w] = __int_as_float(0x7f800000);
         vc[w] = 0;
-        va[w] = -1;
         newp[w] = 0;
     }
     if (depth > 0) {
@@ -413,6 +410,8 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         }
     }
     int ties = 0;
+    U4 tu{0, 0, 0, 0};  // the block of tie draws of steps 4 tblk .. 4 tblk + 3
+    int tblk = -1;
     // A round can only form after the greedy has just taken an X(t) cell (or at the
     // first step past the exclusion phase, or right after a round): when it takes a
     // plain cell instead, every X(t) cell was below the largest plain value, so the
@@ -421,12 +420,10 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
     for (int step = 0; step < n;) {
         const bool use_ex = step < depth;
         if (!use_ex) {
-            int A = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) A += __popc(__ballot_sync(FULL, alive[w]));
+            const int A = n - step;  // columns left
             if (A <= kTailCols) {
                 ties += sx_tail<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic, alive,
-                                        pis, swarm, t, zadd, step, A, newp);
+                                        pis, swarm, t, zadd, step, A, tu, tblk, newp);
                 break;
             }
         }
@@ -439,10 +436,9 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
             for (int w = 0; w < NW; ++w)
                 if (alive[w] && !zin[w] && vc[w] == 0) {
-                    const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w]);
+                    const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
                     vm[w] = cm.v;
                     vc[w] = cm.cnt;
-                    va[w] = cm.first;
                 }
             uint32_t lp = 0u;
 #pragma unroll
@@ -504,21 +500,16 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
                     if (!alive[w] || vc[w] == 0) continue;  // rows of the round are never pic[w]
-                    if (vc[w] == 1) {  // its only copy is row va: gone iff va was deleted
-                        if ((dead[va[w] >> 5] >> (va[w] & 31)) & 1u) vc[w] = 0;
-                        continue;
-                    }
-                    const int c = lane + 32 * w;
+                    int cnt = 0;
 #pragma unroll
                     for (int wi = 0; wi < NW; ++wi) {
-                        uint32_t m = gone[wi];
-                        while (m && vc[w] > 0) {
-                            const int r = 32 * wi + __ffs(m) - 1;
-                            m &= m - 1u;
-                            if (VStore<VT>::to_f(tile[r * n + c]) == vm[w] && --vc[w] > 0 && va[w] == r)
-                                va[w] = vnext<VT>(tile, dead, n, c, pic[w], vm[w], r);
-                        }
+                        if (32 * wi >= n) continue;
+                        uint32_t& m = emw(w, wi);
+                        const uint32_t mv = m;
+                        if (mv & gone[wi]) m = mv & ~gone[wi];
+                        cnt += __popc(mv & ~gone[wi]);
                     }
+                    vc[w] = cnt;
                 }
                 step += nb;
                 continue;
@@ -526,38 +517,37 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         }
 
         // ---- one greedy step: the effective maximum of every owned column ----
+        // mode: 0 the X(t) cell alone, 1 the plain maximum and the X(t) cell (equal),
+        // 2 the plain maximum alone
         uint32_t key[NW];
-        int cnt[NW], arg[NW];
+        int cnt[NW], mode[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             key[w] = 0u;
             cnt[w] = 0;
-            arg[w] = -1;
+            mode[w] = 0;
             if (!alive[w]) continue;
             if (vc[w] == 0 && !(zin[w] && zv[w] > vm[w])) {
-                const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w]);
+                const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
                 vm[w] = cm.v;
                 vc[w] = cm.cnt;
-                va[w] = cm.first;
             }
             float e;
             if (vc[w] == 0) {  // the X(t) cell above a stale bound, or nothing else left
                 if (!zin[w]) continue;
                 e = zv[w];
                 cnt[w] = 1;
-                arg[w] = pic[w];
             } else if (zin[w] && zv[w] > vm[w]) {
                 e = zv[w];
                 cnt[w] = 1;
-                arg[w] = pic[w];
             } else if (zin[w] && zv[w] == vm[w]) {
                 e = vm[w];
                 cnt[w] = vc[w] + 1;
-                arg[w] = min(va[w], pic[w]);
+                mode[w] = 1;
             } else {
                 e = vm[w];
                 cnt[w] = vc[w];
-                arg[w] = va[w];
+                mode[w] = 2;
             }
             key[w] = fkey(e);
         }
@@ -594,8 +584,11 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             int k = 0;
             ++ties;
             if (s.tie_rule == 0) {
-                const U4 u = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
-                k = (int)below(word_of(u, step & 3), (uint32_t)tot);
+                if ((step >> 2) != tblk) {  // one block of draws serves four steps
+                    tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                    tblk = step >> 2;
+                }
+                k = (int)below(word_of(tu, step & 3), (uint32_t)tot);
             }
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
@@ -618,15 +611,31 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                 }
             }
         }
-        // the owner takes the kk-th row (ascending) holding its column's maximum
+        // the owner takes the kk-th row (ascending) holding its column's maximum: the
+        // rows of the mask, with the X(t) row when its cell is equal (mode 1)
         int r = -1, took_x = 0;
         if (lane == owner) {
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 if (w != ow) continue;
-                r = arg[w];
-                if (kk > 0)  // several copies: the plain maximum, maybe tied with the X(t) cell
-                    r = kth_row<VT>(tile, dead, n, lane + 32 * w, pic[w], zin[w], zv[w], vm[w], kk);
+                if (mode[w] == 0) {
+                    r = pic[w];
+                } else {
+                    int k = kk;
+#pragma unroll
+                    for (int wi = 0; wi < NW; ++wi) {
+                        if (r >= 0 || 32 * wi >= n) continue;
+                        uint32_t m = emw(w, wi);
+                        if (mode[w] == 1 && (pic[w] >> 5) == wi) m |= 1u << (pic[w] & 31);
+                        const int c = __popc(m);
+                        if (k < c) {
+                            for (int j = 0; j < k; ++j) m &= m - 1u;  // drop the k lower rows
+                            r = 32 * wi + __ffs(m) - 1;
+                        } else {
+                            k -= c;
+                        }
+                    }
+                }
                 newp[w] = r;
                 alive[w] = false;
                 took_x = (zin[w] && r == pic[w]) ? 1 : 0;
@@ -647,9 +656,13 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             if (!alive[w]) continue;
             if (r == pic[w]) {
                 zal[w] = false;
-            } else if (vc[w] > 0 && VStore<VT>::to_f(tile[r * n + lane + 32 * w]) == vm[w]) {
-                if (--vc[w] > 0 && va[w] == r)
-                    va[w] = vnext<VT>(tile, dead, n, lane + 32 * w, pic[w], vm[w], r);
+            } else if (vc[w] > 0) {
+                uint32_t& m = emw(w, r >> 5);
+                const uint32_t bit = 1u << (r & 31), mv = m;
+                if (mv & bit) {
+                    m = mv & ~bit;
+                    --vc[w];
+                }
             }
         }
         ++step;
@@ -959,6 +972,8 @@ __global__ void __launch_bounds__(kWarps * 32)
     unsigned char* wbase = smem + kBarBytes + warp * warp_bytes<VT>(n_max);
     VT* tile = reinterpret_cast<VT*>(wbase);
     uint32_t* dead = reinterpret_cast<uint32_t*>(wbase + tile_bytes<VT>(n_max));
+    uint32_t* em = reinterpret_cast<uint32_t*>(wbase + tile_bytes<VT>(n_max) + 32 + lists_bytes(n_max));
+    const int nwr = (n_max + 31) >> 5;
     if (lane == 0) mbar_init(bar, 1);
     __syncwarp();
     uint32_t phase = 0;
@@ -1000,7 +1015,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int ties = s.sx_kind == 1
                              ? pick_column<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic,
                                                    pis, swarm, t, zadd, newp)
-                             : second_target<NW, VT>(s, tile, dead, n, lane, pic, pis, swarm, t, zadd, newp);
+                             : second_target<NW, VT>(s, tile, dead, em, nwr, n, lane, pic, pis, swarm, t, zadd,
+                                                     newp);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;

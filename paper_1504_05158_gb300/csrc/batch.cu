@@ -185,7 +185,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     b->m_max = m_max;
     int kind_count[LS_KINDS] = {};
     for (auto* s : b->members) ++kind_count[s->ls_iter.kind];
-    size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024;
+    size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024 + 256;
     for (int k = 0; k < LS_KINDS; ++k) bytes += (sizeof(LsArgs) + sizeof(int32_t)) * kind_count[k] + 512;
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, bytes);
@@ -202,6 +202,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     };
     b->d_views = (StateView*)take(sizeof(StateView) * count);
     b->d_prefix = (int32_t*)take(sizeof(int32_t) * (count + 1));
+    int32_t* d_pos_work = (int32_t*)take(sizeof(int32_t));
     e = cudaMemcpy(b->d_views, b->h_views.data(), sizeof(StateView) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_prefix, b->h_prefix.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice);
@@ -226,7 +227,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     int any_old = 0, any_new = 0;
     for (int i = 0; i < count; ++i) (params[i].pos_uses_new_v ? any_new : any_old) = 1;
     b->vsx = VsxLaunch{b->d_views, b->d_prefix, count, n_max, total,
-                       params[0].v_storage == PSO_V_BF16, 0, any_old, any_new};
+                       params[0].v_storage == PSO_V_BF16, 0, any_old, any_new, d_pos_work};
     if (e == cudaSuccess && autotune_shapes) {
         e = autotune(b);
         // the tuning runs advanced the members: start them again from their seeds

@@ -466,7 +466,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
                     for (int w0 = 0; w0 < w; ++w0) {
                         const uint32_t mk = inB[w0] ? bkey[w0] : 0xFFFFFFFFu;
-#pragma unroll 1
+#pragma unroll 8
                         for (int L = 0; L < 32; ++L)
                             if (__shfl_sync(FULL, mk, L) == bkey[w]) first = false;
                     }
@@ -555,36 +555,72 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
         for (int w = 0; w < NW; ++w) lm = max(lm, key[w]);
         const uint32_t gm = __reduce_max_sync(FULL, lm);
-        // |M| = 1 iff exactly one column holds the maximum, once
-        unsigned hit[NW];
-        int nhit = 0;
-        bool multi = false;
+        // the elements of M per column (c = lane + 32 w ascending); while every count
+        // is below 8, three ballots of their low bits give each slot's total and every
+        // lane's inclusive prefix without a shuffle scan
+        int cm[NW];
+        bool big = false;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            hit[w] = __ballot_sync(FULL, key[w] == gm);
-            nhit += __popc(hit[w]);
-            multi = multi || (key[w] == gm && cnt[w] > 1);
+            cm[w] = key[w] == gm ? cnt[w] : 0;
+            big = big || cm[w] >= 8;
         }
-        const bool unique = nhit == 1 && !__any_sync(FULL, multi);
-        // the column holding the k-th element of M (columns c = lane + 32 w ascending)
-        int owner = -1, ow = 0, kk = 0;
-        if (unique) {
+        unsigned b0[NW], b1[NW], b2[NW];
+        int tw[NW], tot = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                if (owner < 0 && hit[w]) {
-                    owner = __ffs(hit[w]) - 1;
-                    ow = w;
+        for (int w = 0; w < NW; ++w) {
+            b0[w] = __ballot_sync(FULL, cm[w] & 1);
+            b1[w] = __ballot_sync(FULL, cm[w] & 2);
+            b2[w] = __ballot_sync(FULL, cm[w] & 4);
+            tw[w] = __popc(b0[w]) + 2 * __popc(b1[w]) + 4 * __popc(b2[w]);
+            tot += tw[w];
+        }
+        const bool wide = __any_sync(FULL, big);
+        int owner = -1, ow = 0, kk = 0;
+        if (!wide) {
+            int k = 0;
+            if (tot > 1) {
+                ++ties;
+                if (s.tie_rule == 0) {
+                    if ((step >> 2) != tblk) {  // one block of draws serves four steps
+                        tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                        tblk = step >> 2;
+                    }
+                    k = (int)below(word_of(tu, step & 3), (uint32_t)tot);
                 }
             }
-        } else {
-            int lc = 0;
+            int sel = -1;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) lc += (key[w] == gm) ? cnt[w] : 0;
-            const int tot = (int)__reduce_add_sync(FULL, (unsigned)lc);
+            for (int w = 0; w < NW; ++w) {
+                if (sel >= 0) continue;
+                if (k < tw[w])
+                    sel = w;
+                else
+                    k -= tw[w];
+            }
+            unsigned B0 = 0u, B1 = 0u, B2 = 0u;
+            int c = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (w == sel) {
+                    B0 = b0[w];
+                    B1 = b1[w];
+                    B2 = b2[w];
+                    c = cm[w];
+                }
+            const unsigned le = (2u << lane) - 1u;  // lanes 0 .. lane
+            const int incl = __popc(B0 & le) + 2 * __popc(B1 & le) + 4 * __popc(B2 & le);
+            owner = __ffs(__ballot_sync(FULL, sel >= 0 && incl > k)) - 1;
+            ow = sel < 0 ? 0 : sel;
+            kk = k - (incl - c);  // used by the owner only
+        } else {
+            tot = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) tot += (int)__reduce_add_sync(FULL, (unsigned)cm[w]);
             int k = 0;
             ++ties;
             if (s.tie_rule == 0) {
-                if ((step >> 2) != tblk) {  // one block of draws serves four steps
+                if ((step >> 2) != tblk) {
                     tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
                     tblk = step >> 2;
                 }
@@ -593,21 +629,21 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 if (owner >= 0) continue;
-                const int c = (key[w] == gm) ? cnt[w] : 0;
+                const int c = cm[w];
                 int incl = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int v = __shfl_up_sync(FULL, incl, o);
                     if (lane >= o) incl += v;
                 }
-                const int tw = __shfl_sync(FULL, incl, 31);
-                if (k < tw) {
+                const int twid = __shfl_sync(FULL, incl, 31);
+                if (k < twid) {
                     const unsigned bal = __ballot_sync(FULL, incl > k);
                     owner = __ffs(bal) - 1;
                     ow = w;
                     kk = __shfl_sync(FULL, k - (incl - c), owner);
                 } else {
-                    k -= tw;
+                    k -= twid;
                 }
             }
         }
@@ -964,7 +1000,8 @@ __global__ void __launch_bounds__(128)
 // with one bulk copy; shared-memory slots are sized for the largest n of the table.
 template <int NW, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
-    k_position(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max) {
+    k_position(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
+               int32_t* __restrict__ work) {
     const int wpc = blockDim.x >> 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -980,7 +1017,15 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int total = prefix[count];
     TableCursor cur;
 
-    for (int f = blockIdx.x * wpc + warp; f < total; f += gridDim.x * wpc) {
+    // particles are handed out one at a time from a counter (their cost varies with
+    // the ties of the greedy), else in a fixed grid-stride order
+    auto grab = [&](int fixed) {
+        if (!work) return fixed;
+        int q = 0;
+        if (lane == 0) q = atomicAdd(work, 1);
+        return __shfl_sync(FULL, q, 0);
+    };
+    for (int f = grab(blockIdx.x * wpc + warp); f < total; f = grab(f + gridDim.x * wpc)) {
         const int p = cur.advance(prefix, count, f);
         const StateView s = views[cur.inst];
         const int n = s.n;
@@ -1043,7 +1088,11 @@ cudaError_t launch_pos(const VsxLaunch& L, cudaStream_t st) {
     const int need = (L.total + wpc - 1) / wpc;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_position<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max);
+    if (L.d_work) {
+        e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_position<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,8 @@ struct VsxLaunch {
     int warps;                // warps per CTA of the position kernel (0 = automatic)
     int has_old_v;            // some population forms X(t) + V(t) (velocity after S_x)
     int has_new_v;            // some population forms X(t) + V(t+1) (velocity first)
+    int32_t* d_work;          // the position kernel's particle counter (zeroed before
+                              // each launch), or null for a fixed grid-stride order
 };
 // S_x of every particle (reads the V tiles, writes Xsx)
 cudaError_t launch_position(const VsxLaunch& L, cudaStream_t st);

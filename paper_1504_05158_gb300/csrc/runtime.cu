@@ -310,7 +310,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     const size_t obest = take(sv.ps), obc = take(8), obi = take(4), ot = take(4);
     const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
-    const size_t owork = take(2 * 4);
+    const size_t owork = take(3 * 4);  // search (iteration, set-up), position
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -365,7 +365,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     s->h_prefix[0] = 0;
     s->h_prefix[1] = P;
     s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0,
-                       params->pos_uses_new_v ? 0 : 1, params->pos_uses_new_v ? 1 : 0};
+                       params->pos_uses_new_v ? 0 : 1, params->pos_uses_new_v ? 1 : 0, s->d_work + 2};
     s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     e = cudaMemsetAsync(base, 0, off, s->stream);

@@ -306,8 +306,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
 // of G, the matrix
 //     H[k][m] = G[k][p(m)] - G[k][p(k)]      (zero diagonal)
 // and the permuted distances Dp[k][m] = D[p(k)][p(m)], so that
-//     delta(k, m) = 2 (H[k][m] + H[m][k]) + 4 F[k][m] Dp[k][m]
-// reads four shared-memory words. A swap (r, s) changes G by the rank-1 term
+//     delta(k, m) = 2 (H[k][m] + H[m][k]) + 4 F[k][m] Dp[k][m];
+// the table stores H + F o Dp (F, Dp symmetric), so that delta(k, m) is twice the
+// sum of two of its words. A swap (r, s) changes G by the rank-1 term
 // fd e^T (fd[k] = F[k][r] - F[k][s], e[x] = Dp[s][x] - Dp[r][x], p before the
 // swap), hence
 //     H[k][m] += fd[k] (e[m] - e[k])                       k, m not in {r, s},
@@ -485,72 +486,114 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
     const int nv = n / 2;
     int moves = 0, rounds = 0;
     if (a.max_moves >= 0) {
+        const int kl = a.key_l, sh = 2 * kl;
+        const int pmask = (1 << kl) - 1;
         for (;;) {
             if (a.max_moves > 0 && moves >= a.max_moves) break;
             if (moves >= kSafetyMoves) {
                 if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
                 break;
             }
-            // (delta << 16) | (k << 8 | m): the minimum is the lowest pair on ties; four
-            // independent running minima keep the dependency chains short
-            long long b0 = LLONG_MAX, b1 = LLONG_MAX, b2 = LLONG_MAX, b3 = LLONG_MAX;
-            if (on) {
-                auto pair_value = [&](int t) -> long long {
-                    const bool c1 = e < n - 1 - t;
-                    const int k = c1 ? t : n - 2 - t;
-                    const int m = c1 ? t + 1 + e : e;
-                    const int d = 2 * (H[k * gs + m] + H[m * gs + k]) +
-                                  4 * (int)sF[k * n + m] * (int)Dp[k * dps + m];
-                    const long long v = (long long)d * 65536 + ((k << 8) | m);
-                    return (c1 || k != t) ? v : LLONG_MAX;  // k == t: the pair is row t's own
-                };
-                int t = ph;
-                for (; t + 3 * nph < nv; t += 4 * nph) {
-                    const long long v0 = pair_value(t), v1 = pair_value(t + nph);
-                    const long long v2 = pair_value(t + 2 * nph), v3 = pair_value(t + 3 * nph);
-                    b0 = v0 < b0 ? v0 : b0;
-                    b1 = v1 < b1 ? v1 : b1;
-                    b2 = v2 < b2 ? v2 : b2;
-                    b3 = v3 < b3 ? v3 : b3;
+            // pair (k, m), k < m, of virtual row t for this thread; S = H[k][m] + H[m][k]
+            // (the swap value is 2 S); k == t on the second half is row t's own pair
+            auto pair_of = [&](int t, int& k, int& m) {
+                const bool first = e < n - 1 - t;
+                k = first ? t : n - 2 - t;
+                m = first ? t + 1 + e : e;
+                return first || k != t;
+            };
+            // the minimum of (S, k, m), lowest pair on ties: 32-bit keys S 2^(2 kl) +
+            // (k << kl | m) when the instance bounds |S| (kl > 0), else 64-bit keys
+            // S 2^16 + (k << 8 | m); four independent running minima per thread
+            int sbest;
+            unsigned bkey;
+            if (kl > 0) {
+                int b0 = INT_MAX, b1 = INT_MAX, b2 = INT_MAX, b3 = INT_MAX;
+                if (on) {
+                    auto pv = [&](int t) -> int {
+                        int k, m;
+                        const bool ok = pair_of(t, k, m);
+                        const int sv = H[k * gs + m] + H[m * gs + k];
+                        const int v = (int)(((unsigned)sv << sh) | (unsigned)((k << kl) | m));
+                        return ok ? v : INT_MAX;
+                    };
+                    int t = ph;
+                    for (; t + 3 * nph < nv; t += 4 * nph) {
+                        b0 = min(b0, pv(t));
+                        b1 = min(b1, pv(t + nph));
+                        b2 = min(b2, pv(t + 2 * nph));
+                        b3 = min(b3, pv(t + 3 * nph));
+                    }
+                    for (; t < nv; t += nph) b0 = min(b0, pv(t));
                 }
-                for (; t < nv; t += nph) {
-                    const long long v0 = pair_value(t);
-                    b0 = v0 < b0 ? v0 : b0;
+                int kv = min(min(b0, b1), min(b2, b3));
+                bkey = 0u;
+                team_min2<WPP>(kv, bkey, xch, rounds & 1, team, lane, wi);
+                sbest = kv == INT_MAX ? INT_MAX : (kv >> sh);
+                bkey = (unsigned)((((kv >> kl) & pmask) << 8) | (kv & pmask));
+            } else {
+                long long b0 = LLONG_MAX, b1 = LLONG_MAX, b2 = LLONG_MAX, b3 = LLONG_MAX;
+                if (on) {
+                    auto pv = [&](int t) -> long long {
+                        int k, m;
+                        const bool ok = pair_of(t, k, m);
+                        const int sv = H[k * gs + m] + H[m * gs + k];
+                        const long long v = (long long)sv * 65536 + ((k << 8) | m);
+                        return ok ? v : LLONG_MAX;
+                    };
+                    int t = ph;
+                    for (; t + 3 * nph < nv; t += 4 * nph) {
+                        const long long v0 = pv(t), v1 = pv(t + nph);
+                        const long long v2 = pv(t + 2 * nph), v3 = pv(t + 3 * nph);
+                        b0 = v0 < b0 ? v0 : b0;
+                        b1 = v1 < b1 ? v1 : b1;
+                        b2 = v2 < b2 ? v2 : b2;
+                        b3 = v3 < b3 ? v3 : b3;
+                    }
+                    for (; t < nv; t += nph) {
+                        const long long v0 = pv(t);
+                        b0 = v0 < b0 ? v0 : b0;
+                    }
                 }
+                b0 = b1 < b0 ? b1 : b0;
+                b2 = b3 < b2 ? b3 : b2;
+                const long long bv = b2 < b0 ? b2 : b0;
+                sbest = bv == LLONG_MAX ? INT_MAX : (int)(bv >> 16);
+                bkey = bv == LLONG_MAX ? 0xFFFFFFFFu : (unsigned)(bv & 0xFFFF);
+                team_min2<WPP>(sbest, bkey, xch, rounds & 1, team, lane, wi);
             }
-            b0 = b1 < b0 ? b1 : b0;
-            b2 = b3 < b2 ? b3 : b2;
-            const long long bv = b2 < b0 ? b2 : b0;
-            int best = (int)(bv >> 16);
-            unsigned bkey = bv == LLONG_MAX ? 0xFFFFFFFFu : (unsigned)(bv & 0xFFFF);
-            if (bv == LLONG_MAX) best = INT_MAX;
-            team_min2<WPP>(best, bkey, xch, rounds & 1, team, lane, wi);
             ++rounds;
-            if (best >= 0) break;
+            if (sbest >= 0) break;
+            const int best = 2 * sbest;
             const int r = (int)(bkey >> 8), s = (int)(bkey & 255u);
             if (r >= n || s >= n || r >= s) {  // cannot happen; never index with it
                 if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
                 break;
             }
-            // A: the move's vectors and the old rows and columns r, s
+            // A: the move's vectors and the old rows and columns r, s of H (the table
+            // holds H + F o Dp)
             const int Frs = sF[r * n + s], Drs = Dp[r * dps + s];
-            const int hrs = H[r * gs + s], hsr = H[s * gs + r];
-            int fx = 0, ex = 0, drx = 0, dsx = 0, hxr = 0, hxs = 0, hrx = 0, hsx = 0;
+            const int frd = Frs * Drs;
+            const int hrs = H[r * gs + s] - frd, hsr = H[s * gs + r] - frd;
+            int fx = 0, ex = 0, drx = 0, dsx = 0, hxr = 0, hxs = 0, hrx = 0, hsx = 0, Fxr = 0, Fxs = 0;
             const int x = tt;
             if (x < n) {
-                fx = (int)sF[r * n + x] - (int)sF[s * n + x];  // F[x][r] - F[x][s] (symmetric)
+                Fxr = sF[r * n + x];  // F[x][r] (symmetric)
+                Fxs = sF[s * n + x];
+                fx = Fxr - Fxs;
                 drx = Dp[r * dps + x];
                 dsx = Dp[s * dps + x];
                 ex = dsx - drx;
-                hxr = H[x * gs + r];
-                hxs = H[x * gs + s];
-                hrx = H[r * gs + x];
-                hsx = H[s * gs + x];
+                hxr = H[x * gs + r] - Fxr * drx;
+                hxs = H[x * gs + s] - Fxs * dsx;
+                hrx = H[r * gs + x] - Fxr * drx;
+                hsx = H[s * gs + x] - Fxs * dsx;
                 fdv[x] = make_int2((x == r || x == s) ? 0 : fx, fx * ex);
                 ev[x] = ex;
             }
             team_sync<WPP>(team);
-            // B: rows and columns outside {r, s}; rows with fd = 0 do not change
+            // B: rows and columns outside {r, s} (F o Dp does not change there); rows
+            // with fd = 0 do not change
             if (on && e != r && e != s) {
                 const int ec = ev[e];
                 int k = ph;
@@ -571,20 +614,21 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
                     if (q.x) H[k * gs + e] += q.x * ec - q.y;
                 }
             }
-            // C: rows and columns r and s (e[r] = Drs, e[s] = -Drs, fd[r] = -Frs, fd[s] = Frs)
+            // C: rows and columns r and s (e[r] = Drs, e[s] = -Drs, fd[r] = -Frs,
+            // fd[s] = Frs), each with F o Dp of the swapped Dp (Dp[x][r] <- Dp[x][s])
             if (x < n && x != r && x != s) {
-                H[x * gs + r] = hxs - fx * (Drs + ex);
-                H[x * gs + s] = hxr + fx * (Drs - ex);
-                H[r * gs + x] = hrx - hrs - Frs * (ex + Drs);
-                H[s * gs + x] = hsx - hsr + Frs * (ex - Drs);
+                H[x * gs + r] = hxs - fx * (Drs + ex) + Fxr * dsx;
+                H[x * gs + s] = hxr + fx * (Drs - ex) + Fxs * drx;
+                H[r * gs + x] = hrx - hrs - Frs * (ex + Drs) + Fxr * dsx;
+                H[s * gs + x] = hsx - hsr + Frs * (ex - Drs) + Fxs * drx;
                 Dp[x * dps + r] = (ET)dsx;
                 Dp[x * dps + s] = (ET)drx;
                 Dp[r * dps + x] = (ET)dsx;
                 Dp[s * dps + x] = (ET)drx;
             }
             if (tt == 0) {
-                H[r * gs + s] = -hrs - 2 * Frs * Drs;
-                H[s * gs + r] = -hsr - 2 * Frs * Drs;
+                H[r * gs + s] = -hrs - frd;  // -hrs - 2 Frs Drs, plus F[r][s] Dp[r][s] (unchanged)
+                H[s * gs + r] = -hsr - frd;
                 const uint8_t t8 = pi8[r];
                 pi8[r] = pi8[s];
                 pi8[s] = t8;
@@ -781,8 +825,9 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         long long part = 0;
         for (int m = tt; m < n; m += TT) part += ev[m];
         const long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, tt >> 5);
+        // the table holds H + F o Dp, so that a swap value reads two words
         if (ph < nph && col < n)
-            for (int k = ph; k < n; k += nph) H[k * gs + col] -= ev[k];
+            for (int k = ph; k < n; k += nph) H[k * gs + col] += (int)sF[k * n + col] * (int)Dp[k * dps + col] - ev[k];
         team_sync<WPP>(team);
         descend_team<WPP, ET>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
         team_sync<WPP>(team);

@@ -36,6 +36,8 @@ struct LsArgs {
                        // tensor-core search is exact
     int32_t* work;     // device counter handing out this population's particles (zeroed
                        // by the launcher before every launch)
+    int32_t key_l;     // > 0: n <= 2^key_l and n max_f max_d < 2^(30 - 2 key_l), so the
+                       // tensor-core search packs a swap value and its pair in 32 bits
 };
 
 // Which local-search kernel serves a population, and the launch shape.

@@ -78,6 +78,7 @@ LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work) {
     a.counters = init ? nullptr : s->sv.counters;
     a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
     a.tc_exact = s->inst->tc_exact;
+    a.key_l = s->inst->key_l;
     a.work = work;
     return a;
 }
@@ -205,6 +206,14 @@ int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_insta
     if (q->tc_exact && mf <= 255 && md <= 255) q->tc_exact |= 2;
     if (!sym && n <= 128 && mf <= 2048 && md <= 2048 && 2.0L * n * mf * md < (long double)(1 << 24))
         q->tc_exact |= 4;  // the general search
+    // symmetric, zero diagonal: |delta(r, s)| <= 2 (n - 2) max_f max_d, so half of it
+    // (S) with the pair index (2 L bits, n <= 2^L) fits a 32-bit key when
+    // n max_f max_d < 2^(30 - 2 L)
+    {
+        int L = 1;
+        while ((1 << L) < n) ++L;
+        q->key_l = (sym && 2 * L <= 16 && (long double)n * mf * md < (long double)(1u << (30 - 2 * L))) ? L : 0;
+    }
     const size_t bytes = (size_t)n * n * 4;
     cudaError_t e = cudaMalloc(&q->dF, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&q->dD, bytes);
@@ -690,6 +699,7 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
         a.rounds = dr;
         a.max_moves = max_moves;
         a.tc_exact = inst->tc_exact;
+        a.key_l = inst->key_l;
         a.work = dw;
         LsArgs* da = nullptr;
         e = cudaMalloc(&da, sizeof(LsArgs));

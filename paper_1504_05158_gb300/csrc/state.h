@@ -16,6 +16,7 @@ struct qap_instance {
     int32_t exact32;
     int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
     int32_t tc_exact;   // bit 0: the tensor-core set-up of the local search is exact; bit 1: and 8-bit staging fits
+    int32_t key_l;      // pair-index bits of the 32-bit search keys, 0 when |delta| is not bounded enough
 };
 
 // One population. Its kernels read it through one-entry device tables (the same

@@ -745,42 +745,50 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         if (p >= a.count) break;
         for (int m = tt; m < KP; m += TT) pi8[m] = m < n ? a.in[(size_t)p * a.ps_in + m] : 0;
         team_sync<WPP>(team);
-        // Dp (uint16 rows) and the B tile (fp16, zero padded) of this particle
-        for (int i = tt; i < L.NP * (KP / 8); i += TT) {
-            const int m = i / (KP / 8), c = (i % (KP / 8)) * 8;
-            uint32_t h[4] = {0u, 0u, 0u, 0u};
-            if (m < n) {
-                const uint2 pj = *reinterpret_cast<const uint2*>(pi8 + c);
-                const int pm = pi8[m];
-                int v[8];
+        // Dp (ET rows) and the B tile (fp16, zero padded) of this particle. Dp is
+        // symmetric, so thread (part, j) gathers column j of Dp, D[p(m)][p(j)] for the
+        // rows m of its chunks (a warp reads one row of D at distinct columns), and
+        // writes it as row j of Dp and of the B tile
+        {
+            const int parts = TT / L.NP;  // threads per row (NP <= TT)
+            if (tt < parts * L.NP) {
+                const int j = tt % L.NP, part = tt / L.NP;
+                const int pjv = j < n ? (int)pi8[j] : 0;
+                for (int c = 8 * part; c < KP; c += 8 * parts) {
+                    uint32_t h[4] = {0u, 0u, 0u, 0u};
+                    if (j < n) {
+                        const uint2 pm8 = *reinterpret_cast<const uint2*>(pi8 + c);
+                        int v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int pjq = (int)(((q < 4 ? pj.x : pj.y) >> (8 * (q & 3))) & 0xFFu);
-                    v[q] = 0;
-                    if (c + q < n) v[q] = L.smem_d ? (int)sD[pm * n + pjq] : __ldg(a.D + pm * n + pjq);
-                }
+                        for (int q = 0; q < 8; ++q) {
+                            const int pmq = (int)(((q < 4 ? pm8.x : pm8.y) >> (8 * (q & 3))) & 0xFFu);
+                            v[q] = 0;
+                            if (c + q < n) v[q] = L.smem_d ? (int)sD[pmq * n + pjv] : __ldg(a.D + pmq * n + pjv);
+                        }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
-                if (c + 8 <= n) {  // whole words of Dp (rows start on 4 bytes)
-                    if (sizeof(ET) == 2) {
+                        for (int q = 0; q < 4; ++q) h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
+                        if (c + 8 <= n) {  // whole words of Dp (rows start on 4 bytes)
+                            if (sizeof(ET) == 2) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            *reinterpret_cast<uint32_t*>(Dp + m * dps + c + 2 * q) =
-                                (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
-                    } else {
+                                for (int q = 0; q < 4; ++q)
+                                    *reinterpret_cast<uint32_t*>(Dp + j * dps + c + 2 * q) =
+                                        (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
+                            } else {
 #pragma unroll
-                        for (int q = 0; q < 2; ++q)
-                            *reinterpret_cast<uint32_t*>(Dp + m * dps + c + 4 * q) =
-                                (uint32_t)v[4 * q] | ((uint32_t)v[4 * q + 1] << 8) | ((uint32_t)v[4 * q + 2] << 16) |
-                                ((uint32_t)v[4 * q + 3] << 24);
+                                for (int q = 0; q < 2; ++q)
+                                    *reinterpret_cast<uint32_t*>(Dp + j * dps + c + 4 * q) =
+                                        (uint32_t)v[4 * q] | ((uint32_t)v[4 * q + 1] << 8) |
+                                        ((uint32_t)v[4 * q + 2] << 16) | ((uint32_t)v[4 * q + 3] << 24);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                if (c + q < n) Dp[j * dps + c + q] = (ET)v[q];
+                        }
                     }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (c + q < n) Dp[m * dps + c + q] = (ET)v[q];
+                    *reinterpret_cast<uint4*>(U + tc::tile_offset(j, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
                 }
             }
-            *reinterpret_cast<uint4*>(U + tc::tile_offset(m, c, KP)) = make_uint4(h[0], h[1], h[2], h[3]);
         }
         fence_proxy_async();
         team_sync<WPP>(team);
@@ -801,23 +809,50 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
             break;
         }
         tc::fence_after_sync();
-        // G_p from tensor memory (it overwrites the B tile, which the completed
-        // product no longer reads): reader warp w holds rows k = 32 (w % WPP) + lane
+        // G_p from tensor memory, written as H + F o Dp (it overwrites the B tile,
+        // which the completed product no longer reads): reader warp w holds rows
+        // k = 32 (w % WPP) + lane; their diagonal G[k][p(k)] = G_p[k][k] sits in the
+        // two 16-column chunks that start at the warp's first row. F and Dp are read
+        // by symmetry (row c + q, column k: distinct banks across the lanes).
         if (reader) {
 #pragma unroll
             for (int g = 0; g < team_groups<ET>(); ++g) {
-                const int k = 128 * g + 32 * (warp % WPP) + lane;
+                const int kb = 128 * g + 32 * (warp % WPP), k = kb + lane;
+                const uint32_t tb = tcol + (uint32_t)(g * L.NP) + ((uint32_t)(32 * wq) << 16);
+                float dg = 0.0f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = kb + 16 * h;
+                    if (cc >= L.NP) continue;  // warp-uniform
+                    uint32_t v[16];
+                    tc::tmem_ld16(tb + (uint32_t)cc, v);
+                    tc::tmem_wait_ld();
+                    // element k - cc of v by a select tree on its bits (constant indices)
+                    const int idx = k - cc;
+                    uint32_t t8[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) t8[i] = (idx & 8) ? v[i + 8] : v[i];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t8[i] = (idx & 4) ? t8[i + 4] : t8[i];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) t8[i] = (idx & 2) ? t8[i + 2] : t8[i];
+                    const uint32_t pick = (idx & 1) ? t8[1] : t8[0];
+                    if (idx >= 0 && idx < 16) dg = __uint_as_float(pick);
+                }
+                const int d = __float2int_rn(dg);
+                if (k < n) ev[k] = d;
                 for (int c = 0; c < L.NP; c += 16) {
                     uint32_t v[16];
-                    tc::tmem_ld16(tcol + (uint32_t)(g * L.NP) + ((uint32_t)(32 * wq) << 16) + (uint32_t)c, v);
+                    tc::tmem_ld16(tb + (uint32_t)c, v);
                     tc::tmem_wait_ld();
                     if (k < n) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q)
-                            if (c + q < n) H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q]));
+                            if (c + q < n)
+                                H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q])) - d +
+                                                    (int)sF[(c + q) * n + k] * (int)Dp[(c + q) * dps + k];
                     }
                 }
-                if (k < n) ev[k] = H[k * gs + k];  // G[k][p(k)]
             }
         }
         tc::fence_before_sync();
@@ -825,9 +860,6 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         long long part = 0;
         for (int m = tt; m < n; m += TT) part += ev[m];
         const long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, tt >> 5);
-        // the table holds H + F o Dp, so that a swap value reads two words
-        if (ph < nph && col < n)
-            for (int k = ph; k < n; k += nph) H[k * gs + col] += (int)sF[k * n + col] * (int)Dp[k * dps + col] - ev[k];
         team_sync<WPP>(team);
         descend_team<WPP, ET>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
         team_sync<WPP>(team);

@@ -107,7 +107,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one launch of each kernel on this workload, from one
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum); set to None
 # when the kernel changes
-PROFILED_TRAFFIC = {"cost_ls": 812032, "position_sx": 172498944, "velocity": 276134656}
+PROFILED_TRAFFIC = {"cost_ls": 816640, "position_sx": 172775424, "velocity": 276119040}
 
 
 def aggregate(units, span_s, dist, torch, device):

@@ -316,7 +316,10 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     const size_t omoves = take((size_t)P * 4), orounds = take((size_t)P * 4);
     const size_t oPG = take((size_t)m * sv.ps), oPG2 = take((size_t)m * sv.ps);
     const size_t ocostG = take((size_t)m * 8), ocostG2 = take((size_t)m * 8);
-    const size_t obest = take(sv.ps), obc = take(8), obi = take(4), ot = take(4);
+    // the best cost, its iteration and the best permutation side by side: pso_best reads
+    // them with one copy
+    const size_t ores = take(16 + (size_t)sv.ps), obc = ores, obi = ores + 8, obest = ores + 16;
+    const size_t ot = take(4);
     const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
     const size_t owork = take(3 * 4);  // search (iteration, set-up), position
@@ -328,6 +331,12 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
         return status_of(e);
     }
     s->dbase = base;
+    e = cudaMallocHost(&s->h_res, 16 + (size_t)sv.ps);  // pinned: pso_best's read-back
+    if (e != cudaSuccess) {
+        s->h_res = nullptr;
+        pso_destroy(s);
+        return status_of(e);
+    }
     sv.V = base + oV;
     sv.X = (uint8_t*)(base + oX);
     sv.Xsx = (uint8_t*)(base + oXsx);
@@ -450,14 +459,15 @@ int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t fl
 int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
     if (!s) return QAP_ERR_INVALID_ARG;
     const int n = s->sv.n;
-    int64_t c = 0;
-    int32_t it = 0;
-    std::vector<uint8_t> p(n);
-    cudaError_t e = cudaMemcpyAsync(&c, s->sv.best_cost, 8, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&it, s->sv.best_iter, 4, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p.data(), s->sv.best, n, cudaMemcpyDeviceToHost, s->stream);
+    // cost (8 bytes), iteration (4), padding (4), permutation (n): one copy
+    cudaError_t e = cudaMemcpyAsync(s->h_res, s->sv.best_cost, 16 + (size_t)n, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return status_of(e);
+    int64_t c = 0;
+    int32_t it = 0;
+    std::memcpy(&c, s->h_res, 8);
+    std::memcpy(&it, s->h_res + 8, 4);
+    const uint8_t* p = s->h_res + 16;
     if (cost) *cost = c;
     if (iter_found) *iter_found = it;
     if (perm)
@@ -528,6 +538,7 @@ void pso_destroy(pso_state_t s) {
     if (s->g1) cudaGraphExecDestroy(s->g1);
     if (s->g16) cudaGraphExecDestroy(s->g16);
     cudaFree(s->dbase);
+    if (s->h_res) cudaFreeHost(s->h_res);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -41,6 +41,7 @@ struct pso_state {
     qap::VsxLaunch vsx;
     qap::LsLaunch ls_iter, ls_init;
     cudaGraphExec_t g1, g16;
+    unsigned char* h_res;     // pinned: best cost, iteration and permutation (pso_best)
 };
 
 namespace qap {

@@ -81,6 +81,49 @@ def test_discretize_matches_oracle(Q, n, rule, depth, tie, quantised):
         assert sorted(got[i]) == list(range(n))
 
 
+def _ys_converged(count, n, seed):
+    """Y of a converged swarm under Norm: V is -0.5 at the X(t) cell and +0.5 at one
+    other row of each column, tiny (or zero) elsewhere, so every X(t) cell of Y equals
+    0.5 exactly, as do the largest plain values: most greedy steps see many maxima."""
+    rng = np.random.default_rng(seed)
+    Z = W.random_perms(count, n, seed + 1)
+    V = (rng.uniform(-1.0, 1.0, (count, n, n)) * 1e-20).astype(np.float32)
+    V[rng.random((count, n, n)) < 0.3] = 0.0
+    for i in range(count):
+        for j in range(n):
+            V[i, Z[i, j], j] = -0.5
+            if n > 1:
+                r = int(rng.integers(0, n - 1))
+                V[i, r if r < Z[i, j] else r + 1, j] = 0.5
+    Y = V.copy()
+    for i in range(count):
+        Y[i, Z[i], np.arange(n)] += np.float32(1.0)
+    return Y, Z
+
+
+@pytest.mark.parametrize("n", [2, 9, 33, 64, 100])
+@pytest.mark.parametrize("kind,rule,depth,tie", [(0, 0, 2, 0), (0, 1, 2, 0), (0, 0, 0, 1), (1, 0, 0, 0)])
+def test_discretize_converged_pattern(Q, n, kind, rule, depth, tie):
+    depth = min(depth, n - 1)
+    count = 12
+    Y, Z = _ys_converged(count, n, 300 + n)
+    assert np.all(Y[0, Z[0], np.arange(n)] == np.float32(0.5))
+    seed = 0xC0DE0000 + n
+    swarm = np.arange(count, dtype=np.int32) % 4
+    particle = np.arange(count, dtype=np.int32) * 5
+    t = 77
+    g = Q.default_params(sx_kind=kind, sx_rule=rule, depth=depth, tie_rule=tie)
+    q = O.make_params(sx_kind=kind, sx_rule=rule, depth=depth, tie_rule=tie)
+    got = Q.discretize(Y, Z, g, seed, swarm, particle, t)
+    for i in range(count):
+        if kind == 1:
+            want, _ = O.pick_column(q, Y[i], seed, int(particle[i]), int(swarm[i]), t)
+        else:
+            want, _ = O.second_target(q, Y[i], Z[i], seed, int(particle[i]), int(swarm[i]), t)
+        assert np.array_equal(got[i], want), i
+        assert sorted(got[i]) == list(range(n))
+
+
 def test_discretize_worked_example(Q):
     # the 3 x 3 example of section 3.1 (GlobalMax keeps the stuck particle; the
     # SecondTarget pictures of Eq. 6 under the top-d reading)

@@ -468,7 +468,8 @@ __device__ __forceinline__ long long team_sum64(long long v, long long* xch, int
     return t;
 }
 
-// Best-improvement descent of particle p by one team from a complete H. The team's
+// Best-improvement descent of particle p by one team from a complete table H + F o Dp
+// (called H below). The team's
 // threads form `nph` phases of `slotw` threads: thread (ph, e) evaluates pair slot e
 // of virtual rows ph, ph + nph, ... (row t joined with row n-2-t) and, after a move,
 // updates column e of H in rows ph, ph + nph, ...

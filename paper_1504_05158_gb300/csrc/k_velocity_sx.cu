@@ -14,9 +14,9 @@
 // 1 in Z are ignored (all of them as Algorithm 1 prints, or only the `depth`
 // largest, the reading that reproduces the pictures of Eq. 6). M is ordered by
 // column then row; with random ties the k-th element is taken, k = floor(u |M| /
-// 2^32) with u from Philox. Lanes own columns and keep each column's maximum key
-// and multiplicity over the remaining rows, so a step costs one warp reduction
-// plus the columns whose maximum sat in the deleted row.
+// 2^32) with u from Philox. Lanes own columns and keep each column's maximum, its
+// multiplicity and the rows holding it (a bit mask) over the remaining rows, so a
+// step costs a warp reduction, a few ballots and one mask word per owned column.
 #include <climits>
 
 #include "kernels.h"

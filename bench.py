@@ -107,7 +107,10 @@ class ClockSampler:
 # DRAM bytes (read + write) of one launch of each kernel on this workload, from one
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum); set to None
 # when the kernel changes
-PROFILED_TRAFFIC = {"cost_ls": 816640, "position_sx": 172775424, "velocity": 276119040}
+PROFILED_TRAFFIC = {"cost_ls": None, "position_sx": None, "velocity": None}
+STEADY_FROM = 200      # the steady window starts after this many iterations
+FULL_ITERS = 300       # iterations of the whole configuration
+QUALITY_SEEDS = 8      # seeds of the fp32 / bf16 whole runs
 
 
 def aggregate(units, span_s, dist, torch, device):
@@ -150,6 +153,50 @@ def measure(Q, W, torch, storage, steps, warmup, rank, flush):
     torch.cuda.synchronize()
     s0 = sw.stats()
     return sw, s0, stream
+
+
+def timed_steps(sw, torch, stream, steps, flush, flush_each):
+    """Seconds of `steps` iterations replayed from the captured graphs, CUDA events on
+    the state's stream (the L2 flushed before each iteration when V fits in L2)."""
+    with torch.cuda.stream(stream):
+        pairs = []
+        if flush_each:
+            for _ in range(steps):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                sw.step(1)
+                b.record()
+                pairs.append((a, b))
+        else:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sw.step(steps)
+            b.record()
+            pairs = [(a, b)]
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in pairs) / 1e3
+
+
+def whole_runs(Q, W, torch, storage, seeds, iters, flush):
+    """The whole n = 64 configuration (init excluded, `iters` iterations) for each
+    seed: particle-iterations/s over the run and the final best cost. With bf16 V
+    (84 MB, smaller than L2) the L2 is flushed before every iteration."""
+    inst = W.grid64()
+    gi = Q.Instance(inst.F, inst.D)
+    stream = torch.cuda.Stream()
+    flush_each = SWARMS * SWARM_SIZE * N * N * (4 if storage == Q.V_FP32 else 2) <= L2_BYTES
+    out = []
+    for seed in seeds:
+        sw = Q.Swarm(gi, params(Q, storage), seed=seed, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        span = timed_steps(sw, torch, stream, iters, flush, flush_each)
+        best, _, it = sw.best()
+        out.append({"seed": seed, "best": best, "best_iter": it,
+                    "value": SWARMS * SWARM_SIZE * iters / span})
+        sw.close()
+    gi.close()
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -195,25 +242,8 @@ def run_ours(args, rank, world, local_rank):
         # timed region: K iterations replayed from the captured graphs (the path a
         # pso_step caller takes), CUDA events on the state's stream
         with ClockSampler(torch.cuda.current_device() if world == 1 else local_rank) as clk:
-            with torch.cuda.stream(stream):
-                if flush_each:
-                    pairs = []
-                    for _ in range(args.steps):
-                        flush.fill_(1)
-                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a.record()
-                        sw.step(1)
-                        b.record()
-                        pairs.append((a, b))
-                else:
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record()
-                    sw.step(args.steps)
-                    b.record()
-                    pairs = [(a, b)]
-            torch.cuda.synchronize()
+            span = timed_steps(sw, torch, stream, args.steps, flush, flush_each)
         barrier()
-        span = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
         s1 = sw.stats()
         pits, span = aggregate(SWARMS * SWARM_SIZE * args.steps, span, dist, torch, "cuda")
         dfull = s1["delta_full"] - s0["delta_full"]
@@ -229,6 +259,27 @@ def run_ours(args, rank, world, local_rank):
             N, dmoves / kb, drounds / kb, SWARMS * SWARM_SIZE, SWARMS, 4 if storage == Q.V_FP32 else 2)
         pos_ms, ls_ms, bests_ms, _, vel_ms = (m / kb for m in ms)
         best, _, best_it = sw.best()
+        # the steady window: the same population advanced (untimed) past STEADY_FROM
+        # iterations, where the swarms have converged and S_x meets many equal maxima
+        steady = None
+        if not args.no_steady:
+            done = args.warmup + args.steps + kb
+            if done < STEADY_FROM:
+                sw.step(STEADY_FROM - done)
+            torch.cuda.synchronize()
+            s3 = sw.stats()
+            k_st = max(args.steps, 20)
+            st_span = timed_steps(sw, torch, stream, k_st, flush, flush_each)
+            s4 = sw.stats()
+            ms_st = sw.step_timed(10, flush.data_ptr(), flush.numel())
+            s5 = sw.stats()
+            pit4 = s4["particle_iterations"] - s3["particle_iterations"]
+            steady = {"from_iteration": s3["iteration"], "iterations": k_st,
+                      "value": SWARMS * SWARM_SIZE * k_st / st_span, "ms_per_step": st_span * 1e3 / k_st,
+                      "kernel_ms_per_step": {"velocity": ms_st[4] / 10, "position_sx": ms_st[0] / 10,
+                                             "cost_ls": ms_st[1] / 10, "bests_migration": ms_st[2] / 10},
+                      "sx_ties_per_particle": (s4["sx_ties"] - s3["sx_ties"]) / pit4,
+                      "moves_per_particle": (s5["ls_moves"] - s4["ls_moves"]) / (10 * SWARMS * SWARM_SIZE)}
         results[storage_name] = dict(
             value=pits / span, ms_per_step=span * 1e3 / args.steps,
             delta_evals_per_s=(dfull + dincr) * world / span,
@@ -241,8 +292,35 @@ def run_ours(args, rank, world, local_rank):
             moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * kb), flush_each=flush_each,
             breakdown_iterations=kb,
             best_cost=best, best_iter=best_it, iterations=args.warmup + args.steps,
-            clocks=clk.summary())
+            clocks=clk.summary(), steady=steady)
         sw.close()
+
+    # the whole configuration (300 iterations) over several seeds, fp32 and bf16: the
+    # throughput averaged over entire runs and the final best costs (quality of bf16)
+    full = None
+    if not args.no_quality and world == 1:
+        seeds = [1000 + i for i in range(QUALITY_SEEDS)]
+        full = {"iterations": FULL_ITERS, "seeds": seeds}
+        for name, storage in (("fp32", Q.V_FP32), ("bf16", Q.V_BF16)):
+            runs = whole_runs(Q, W, torch, storage, seeds, FULL_ITERS, flush)
+            bests = np.array([r["best"] for r in runs], np.float64)
+            full[name] = {"value": float(np.mean([r["value"] for r in runs])),
+                          "best": [int(b) for b in bests], "best_mean": float(bests.mean()),
+                          "best_std": float(bests.std(ddof=1)), "best_min": int(bests.min())}
+        full["bf16_vs_fp32_mean"] = full["bf16"]["best_mean"] / full["fp32"]["best_mean"] - 1.0
+        full["target"] = "bf16 mean final best within 0.5 % of fp32"
+        full["within_target"] = abs(full["bf16_vs_fp32_mean"]) <= 0.005
+
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["batch64"] = run_batch(args, quick=True)
+        extras["serve"] = run_serve(args, quick=True)
+    int_peak = None
+    try:
+        mad, add = Q.int32_peak()
+        int_peak = {"mad_tops": mad / 1e12, "add_tops": add / 1e12}
+    except Exception as e:  # measurement helper only
+        int_peak = {"error": str(e)}
 
     # end to end through the C-ABI with host buffers: instance upload, init, K iterations
     # each followed by a read-back of the best cost and permutation
@@ -255,7 +333,16 @@ def run_ours(args, rank, world, local_rank):
         cpu = cpu_baseline(args)
 
     if rank == 0:
-        print(json.dumps(result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops)))
+        if int_peak and "mad_tops" in int_peak:
+            alu_peak_tops = max(int_peak["mad_tops"], int_peak["add_tops"])
+            alu_src = "measured: qap_int32_peak, best of 32-bit multiply-add (2 ops) and add (1 op) lane rates"
+        else:
+            alu_src = "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"
+        line = result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src)
+        line["full_run"] = full
+        line["int32_peak"] = int_peak
+        line.update(extras)
+        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
@@ -284,7 +371,7 @@ def run_e2e(args, Q, W, torch, dist, rank, world):
             "what": "qap_create_instance + pso_init + K x (pso_step(1) + pso_best), host F and D"}
 
 
-def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
+def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src):
     if True:
         r = results["fp32"]
         km = r["kernel_ms"]
@@ -292,7 +379,11 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
             "cost_ls": {"kernel": "k_ls_team (goal function + swap local search)", "bound": "alu",
                         "achieved": r["ls_tops"], "peak": alu_peak_tops, "unit": "Tops/s",
                         "frac": r["ls_tops"] / alu_peak_tops, "traffic": PROFILED_TRAFFIC["cost_ls"],
-                        "peak_source": "derived: 152 SMs x 128 int32 lanes x 2 ops x max SM clock"},
+                        "peak_source": alu_src,
+                        "op_count": "ops of a swap search with a table of swap values, every add, "
+                                    "subtract and multiply one op: n(n-1)/2 for the cost, 3(n-2) per "
+                                    "pair for the table, per accepted move 3(n-2) per pair touching "
+                                    "the swapped positions and 7 per other pair"},
             "position_sx": {"kernel": "k_position (SecondTarget, Algorithm 1)", "bound": "hbm",
                             "achieved": r["pos_gbs"], "peak": hbm_peak, "unit": "GB/s",
                             "frac": r["pos_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["position_sx"],
@@ -315,12 +406,10 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
             "roofline_all": roofs,
             "ls_setup_tensor_tflops": r["ls_tc_tflops"],
             "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
-                                                       "kernel_ms", "vel_gbs", "best_cost")}
+                                                       "kernel_ms", "vel_gbs", "best_cost", "steady")}
                      if "bf16" in results else None),
-            "quality": ({"fp32_best": r["best_cost"], "bf16_best": results["bf16"]["best_cost"],
-                         "bf16_vs_fp32": results["bf16"]["best_cost"] / r["best_cost"] - 1.0,
-                         "iterations": r["iterations"]} if "bf16" in results else None),
             "moves_per_particle_iteration": r["moves_per_pit"],
+            "steady": r["steady"],
             "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
@@ -330,19 +419,23 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops):
 # ----------------------------------------------------------------------- oracle
 
 def oracle_sample(steps, warmup, budget_s=None):
-    """The plain oracle on a bounded sample of the workload: 2 swarms x 32 particles of
-    the same instance and parameters, `warmup` untimed then `steps` timed iterations."""
+    """The oracle as it stands on a bounded sample of the workload: 8 swarms x 64
+    particles of the same instance and parameters, its per-particle iteration spread
+    over every host core (oracle.step_parallel), `warmup` untimed then up to `steps`
+    timed iterations (fewer if the time budget runs out)."""
     from oracle import oracle as O
     from paper_1504_05158_gb300 import workloads as W
     inst = W.grid64()
-    q = O.make_params(swarms=2, swarm_size=32, mig_kind=2, mig_period=RING_PERIOD, depth=2)
+    m, ss = 8, 64
+    cores = os.cpu_count() or 1
+    q = O.make_params(swarms=m, swarm_size=ss, mig_kind=2, mig_period=RING_PERIOD, depth=2)
     s = O.init(q, inst.F, inst.D, 64)
-    O.step(q, inst.F, inst.D, 64, s, warmup)
+    O.step_parallel(q, inst.F, inst.D, 64, s, warmup, threads=cores)
     c0 = s.counters.copy()
     t0 = time.perf_counter()
     done = 0
     for _ in range(steps):
-        O.step(q, inst.F, inst.D, 64, s, 1)
+        O.step_parallel(q, inst.F, inst.D, 64, s, 1, threads=cores)
         done += 1
         if budget_s and time.perf_counter() - t0 > budget_s:
             break
@@ -350,10 +443,11 @@ def oracle_sample(steps, warmup, budget_s=None):
     c1 = s.counters
     pit = int(c1[O.C_PIT] - c0[O.C_PIT])
     dev = int(c1[O.C_DELTA_FULL] + c1[O.C_DELTA_INCR] - c0[O.C_DELTA_FULL] - c0[O.C_DELTA_INCR])
-    return {"value": pit / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "delta_evals_per_s": dev / dt,
-            "sample": f"2 swarms x 32 particles of the same n=64 instance, {done} timed "
-                      f"iterations after {warmup} warm-up, single thread"}
+    return {"value": pit / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "delta_evals_per_s": dev / dt, "steps_done": done, "sample_ms_per_step": 1e3 * dt / done,
+            "sample": f"{m} swarms x {ss} particles of the same n=64 instance, {done} timed "
+                      f"iterations after {warmup} warm-up, the oracle's particle iteration on "
+                      f"{cores} host threads"}
 
 
 def cpu_baseline(args):
@@ -366,11 +460,14 @@ def run_reference(args, rank, world):
     r = oracle_sample(steps=args.steps, warmup=args.warmup, budget_s=120.0)
     cfg = workload_config("fp64 (oracle)")
     cfg["l2"] = "host cores (no GPU)"
-    cfg["timing"] = ("wall clock of each step over a sample of the workload: 2 swarms x 32 particles "
-                     "of the same instance and parameters, scaled to particle-iterations/s")
+    cfg["timing"] = ("wall clock of each step over a sample of the workload (8 swarms x 64 particles "
+                     "of the same instance and parameters), scaled to particle-iterations/s")
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * 64 / r["value"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": r["sample_ms_per_step"],
+            "ms_per_step_is": "the sample's time per iteration (512 particles), not the workload's",
+            "workload_ms_per_step_est": 1e3 * SWARMS * SWARM_SIZE / r["value"],
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg, "impl": "reference",
             "cpu_baseline": {k: r[k] for k in ("kind", "cores", "sample", "value", "unit")},
@@ -382,10 +479,11 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------- other workloads
 
-def run_batch(args):
+def run_batch(args, quick=False):
     """64 instances with n uniform in [20, 128] (half dense uniform, half grid with
     sparse flows), 8 swarms x 256 particles each, bf16 velocity storage, all in one
-    batch (one launch per phase, graph replay, autotuned shapes)."""
+    batch (one launch per phase, graph replay, autotuned shapes). quick: a summary
+    dict for the main line (5 warm-up, 20 timed iterations) instead of a JSON line."""
     import torch
 
     from paper_1504_05158_gb300 import build as B
@@ -396,16 +494,27 @@ def run_batch(args):
     gis = [Q.Instance(i.F, i.D) for i in insts]
     prm = [Q.default_params(swarms=8, swarm_size=256, v_storage=Q.V_BF16) for _ in insts]
     b = Q.Batch(gis, prm, [4096 + i for i in range(len(insts))], autotune=True)
-    b.step(args.warmup)
+    warm, steps = (5, 20) if quick else (args.warmup, args.steps)
+    b.step(warm)
     torch.cuda.synchronize()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    # the whole-batch rate from graph replays (the path pso_batch_step takes), then a
+    # per-phase breakdown launched kernel by kernel
+    stream = torch.cuda.current_stream()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms = b.step_timed(args.steps, flush.data_ptr(), flush.numel())
+        a.record(stream)
+        b.step(steps)
+        z.record(stream)
+        torch.cuda.synchronize()
+    graph_ms = a.elapsed_time(z)
+    ms = b.step_timed(min(steps, 10), flush.data_ptr(), flush.numel())
+    kb = min(steps, 10)
     P = sum(p.swarms * p.swarm_size for p in prm)
     ns = [i.n for i in insts]
-    out = {"metric": "particle-iterations/s, uneven batch", "value": P * args.steps / (ms[3] / 1e3),
-           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms[3] / args.steps, "higher_is_better": True, "dtype": "f32 (bf16 V)",
+    out = {"metric": "particle-iterations/s, uneven batch", "value": P * steps / (graph_ms / 1e3),
+           "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+           "ms_per_step": graph_ms / steps, "higher_is_better": True, "dtype": "f32 (bf16 V)",
            "data": "synthetic",
            "config": {"workload": "64 instances, n uniform in [20, 128], 8 x 256 particles each, bf16 V",
                       "n_min": min(ns), "n_max": max(ns), "particles": P,
@@ -413,24 +522,34 @@ def run_batch(args):
                                      "team2 (n<=64)": sum(32 < n <= 64 for n in ns),
                                      "team8 (n<=128)": sum(64 < n <= 128 for n in ns),
                                      "simt (n>128)": sum(n > 128 for n in ns)}},
-           "kernel_ms_per_step": {"velocity": ms[4] / args.steps, "position_sx": ms[0] / args.steps,
-                                  "cost_ls": ms[1] / args.steps, "bests_migration": ms[2] / args.steps},
+           "kernel_ms_per_step": {"velocity": ms[4] / kb, "position_sx": ms[0] / kb,
+                                  "cost_ls": ms[1] / kb, "bests_migration": ms[2] / kb},
+           "timing": "value: graph replays of the whole batch, CUDA events; kernel_ms_per_step: "
+                     "further iterations launched kernel by kernel, L2 flushed before each",
            "clocks": clk.summary(), "gpu_launches": None}
-    print(json.dumps(out))
     b.close()
+    for g in gis:
+        g.close()
+    if quick:
+        return {k: out[k] for k in ("value", "ms_per_step", "steps", "warmup", "config", "kernel_ms_per_step",
+                                    "timing")}
+    print(json.dumps(out))
 
 
-def run_serve(args):
+def run_serve(args, quick=False):
     """Poisson arrivals at args.rate requests/s for args.duration s; each request a
     fresh instance with n in {32, 64, 100, 150}, 4 096-16 384 particles in 8-32
-    swarms, 150 iterations; admitted under a 120 GB device-memory budget."""
+    swarms, 150 iterations; admitted under a 120 GB device-memory budget. quick: the
+    first args.serve_quick_s seconds of the same stream, as a summary dict for the
+    main line."""
     import torch
 
     from paper_1504_05158_gb300 import build as B
     B.build()
     from paper_1504_05158_gb300 import serve as S
     from paper_1504_05158_gb300 import workloads as W
-    reqs = W.serving_stream(rate_hz=args.rate, duration_s=args.duration, iterations=args.serve_iters)
+    duration = args.serve_quick_s if quick else args.duration
+    reqs = W.serving_stream(rate_hz=args.rate, duration_s=duration, iterations=args.serve_iters)
     jobs = S.jobs_from_stream(reqs)
     torch.cuda.synchronize()
     srv = S.Server(budget_bytes=120 * 10**9, inflight_particles=args.inflight)
@@ -439,13 +558,18 @@ def run_serve(args):
     summ = rep.summary()
     out = {"metric": "serving: latency p50/p99 and aggregate particle-iterations/s", "unit": UNIT,
            "value": summ["particle_iterations_per_s"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
-           "requests": summ["requests"], "makespan_s": summ["makespan_s"],
+           "requests": summ["requests"], "failed": summ["failed"], "makespan_s": summ["makespan_s"],
            "peak_bytes": summ["peak_bytes"], "peak_slots": summ["peak_slots"],
            "peak_inflight_particles": summ["peak_inflight_particles"],
-           "config": {"workload": f"Poisson {args.rate}/s for {args.duration} s, n in {{32,64,100,150}}, "
+           "config": {"workload": f"Poisson {args.rate}/s for {duration} s, n in {{32,64,100,150}}, "
                                   f"4096-16384 particles, {args.serve_iters} iterations, 120 GB budget",
-                      "inflight_particles": args.inflight},
+                      "inflight_particles": args.inflight,
+                      "latency": "arrival to read-back of the best solution"},
            "higher_is_better": True, "data": "synthetic", "clocks": clk.summary()}
+    if quick:
+        out["config"]["note"] = (f"the first {duration} s of arrivals of the 60 s stream: the whole stream asks "
+                                 "for several times what one GPU delivers, so latency is mostly queueing")
+        return {k: out[k] for k in ("value", "p50_s", "p99_s", "requests", "failed", "makespan_s", "config")}
     print(json.dumps(out))
 
 
@@ -457,6 +581,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-steady", action="store_true", help="skip the steady window (iterations 200+)")
+    ap.add_argument("--no-quality", action="store_true", help="skip the whole 300-iteration fp32/bf16 runs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving summaries")
+    ap.add_argument("--serve-quick-s", type=float, default=2.0,
+                    help="seconds of arrivals of the serving summary on the main line")
     ap.add_argument("--variants", default="fp32,bf16",
                     help="velocity storage formats to time (fp32 is the headline)")
     ap.add_argument("--workload", choices=("grid64", "batch64", "serve"), default="grid64",

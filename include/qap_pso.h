@@ -68,6 +68,8 @@ typedef struct {
     int32_t symmetric_zero_diag; /* 1 if F and D are both symmetric with zero diagonal */
     int32_t max_f, max_d;        /* largest entries */
     int32_t exact_int32;         /* 1 if n * max_f * max_d < 2^27 (all swap values fit int32) */
+    int32_t exact_int64;         /* 1 if (n^2 + 8 n + 4) * max_f * max_d < 2^62: every cost and
+                                    swap value fits int64, so the instance can be solved */
 } qap_instance_info_t;
 int qap_instance_info(qap_instance_t inst, qap_instance_info_t* out);
 
@@ -117,17 +119,23 @@ typedef struct pso_state* pso_state_t;
  * section 3.3): X(0) by a Fisher-Yates shuffle and V(0) uniform in
  * [-v_max, v_max), both from Philox; cost, P^L = X(0), P^G and the global best.
  * `stream` is a cudaStream_t (NULL = a new stream owned by the state). The state
- * keeps a pointer to `inst`, which must outlive it. Errors: QAP_ERR_INVALID_ARG
- * (bad parameters), QAP_ERR_UNSUPPORTED (local search requested on a general
- * instance — not symmetric, or with a nonzero diagonal — whose entries exceed 2048,
- * 2 n max_f max_d >= 2^24 or n > 128; or n above the device limit),
- * QAP_ERR_OVERFLOW (values too large for the exact int32 path), QAP_ERR_OOM,
+ * keeps a pointer to `inst`, which must outlive it. Every instance whose costs
+ * fit int64 (qap_instance_info_t.exact_int64) is solved exactly: the search kernel
+ * is chosen by the instance (tensor-core set-up for small entries, int32 or int64
+ * SIMT arithmetic otherwise, the general O(n) swap formula for asymmetric
+ * instances with large entries). Errors: QAP_ERR_INVALID_ARG (bad parameters),
+ * QAP_ERR_UNSUPPORTED (n above the velocity kernels' shared-memory limit),
+ * QAP_ERR_OVERFLOW (a cost or swap value could leave int64), QAP_ERR_OOM,
  * QAP_ERR_CUDA. */
 int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, void* stream,
              pso_state_t* out);
 
 /* Queues `iterations` (>= 0) full iterations on the state's stream and returns
- * without waiting. Iterations are replayed from a captured CUDA graph. */
+ * without waiting: each is the iteration of section 3.1 and 3.2 (Eq. 4, Eq. 5 with
+ * SecondTarget of Algorithm 1, the goal function of Eq. 1, the swap local search,
+ * P^L, P^G, the global best, migration by Algorithm 2 or the ring) for every
+ * particle. Iterations are replayed from a captured CUDA graph. A failure inside a
+ * kernel (a bounded wait that gave up) is reported by the next pso_best. */
 int pso_step(pso_state_t st, int32_t iterations);
 
 /* Like pso_step, but launches each kernel of every iteration directly (no graph)
@@ -149,9 +157,13 @@ int pso_footprint(int32_t n, const pso_params_t* params, size_t* bytes);
  * 0 (never waits). */
 int pso_poll(pso_state_t st, int32_t* done);
 
-/* Best solution found so far (synchronises): its cost, its permutation (n
+/* Best solution found so far (synchronises): its cost (Eq. 1), its permutation (n
  * entries, may be NULL) and the number of completed iterations when it was found
- * (0 = during initialisation). */
+ * (0 = during initialisation). The paper keeps this best on the host (section 3.3);
+ * here it lives on the device and is read back in one copy together with the
+ * kernels' error counter. Errors: QAP_ERR_TIMEOUT when any kernel of this state
+ * gave up a bounded wait or skipped an inconsistent access (the results may then
+ * be incomplete; outputs are left untouched), QAP_ERR_CUDA. */
 int pso_best(pso_state_t st, int64_t* cost, int32_t* perm, int32_t* iter_found);
 
 typedef struct {
@@ -160,7 +172,8 @@ typedef struct {
     int64_t best_cost;      /* global best ever */
     int64_t min, p5, p25, p50, p75, max; /* current costs, nearest-rank percentiles
                                             (section 4.2) */
-    double mean;
+    double mean;            /* the exact integer sum of the current costs (summed on the
+                               device in 128 bits) divided by their count on the host */
     int64_t particle_iterations; /* counters since pso_init */
     int64_t ls_moves, ls_rounds;
     int64_t delta_full;     /* swap values formed from a fresh O(n^3) set-up (first round) */
@@ -241,17 +254,41 @@ void pso_batch_destroy(pso_batch_t b);
 
 /* ------------------------------------------------ single-kernel entry points */
 /* Goal function (Eq. 1) of `count` permutations (host, count x n int32) on the
- * device; out: count int64. */
+ * device; out: count int64. Any instance whose costs fit int64 (else
+ * QAP_ERR_OVERFLOW). */
 int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int64_t* out);
 
 /* Best-improvement swap local search (the search of every iteration) on `count`
  * permutations (host, count x n int32, improved in place), max_moves as
- * pso_params_t.ls_max_moves (>= 0). Outputs (host, count entries each, any may be
- * NULL): final costs, moves, rounds (neighbourhood evaluations). General instances
- * (not symmetric, or with a nonzero diagonal) need entries <= 2048,
- * 2 n max_f max_d < 2^24 and n <= 128 (else QAP_ERR_UNSUPPORTED). */
+ * pso_params_t.ls_max_moves (>= 0). The paper defines no local search (section 4.2
+ * only says that PSO searches a local neighbourhood); this one is the swap
+ * neighbourhood {p o (r s)} searched best-improvement: the smallest swap value,
+ * the lowest pair (r, s) in r-major order on ties, applied while negative, until
+ * no swap improves or max_moves moves were made. Outputs (host, count entries
+ * each, any may be NULL): final costs, moves, rounds (neighbourhood evaluations).
+ * Any instance whose costs fit int64; errors: QAP_ERR_OVERFLOW otherwise. */
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds);
+
+/* The goal function (max_moves < 0; perms are left unchanged and costs must not
+ * be NULL) or the local search above (max_moves >= 0), on the search kernel named
+ * by `kernel` instead of the automatic choice, so that the kernels can be compared
+ * with each other:
+ *   QAP_SEARCH_AUTO    the kernel pso_step uses for this instance;
+ *   QAP_SEARCH_TENSOR  the tensor-core set-up (symmetric with zero diagonal: entries
+ *                      <= 2048, n max_f max_d < 2^24, n <= 128, or n <= 160 with
+ *                      entries <= 255; general: entries <= 2048, 2 n max_f max_d < 2^24,
+ *                      n <= 128);
+ *   QAP_SEARCH_SIMT    int32 SIMT set-up (symmetric, n max_f max_d < 2^27, D <= 65535);
+ *   QAP_SEARCH_INT64   int64 arithmetic (the int64 SIMT set-up for symmetric
+ *                      instances that fit it, else the direct kernel);
+ *   QAP_SEARCH_DIRECT  every swap value from the general O(n) formula, int64.
+ * Errors: QAP_ERR_UNSUPPORTED when the named kernel is not exact for the instance
+ * or does not serve its n; QAP_ERR_OVERFLOW, QAP_ERR_INVALID_ARG as above. */
+enum { QAP_SEARCH_AUTO = 0, QAP_SEARCH_TENSOR = 1, QAP_SEARCH_SIMT = 2, QAP_SEARCH_INT64 = 3,
+       QAP_SEARCH_DIRECT = 4 };
+int qap_search_with(qap_instance_t inst, int32_t kernel, int32_t* perms, int32_t count, int32_t max_moves,
+                    int64_t* costs, int32_t* moves, int32_t* rounds);
 
 /* Swap values of one permutation: out[idx(r, s)] = f(p o (r s)) - f(p) for every
  * pair r < s, in r-major order (idx = r n - r (r + 1) / 2 + s - r - 1), by the
@@ -278,6 +315,16 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
                    uint64_t seed, const int32_t* swarm, const int32_t* particle, int32_t t,
                    int32_t* out_perm);
 
+/* ------------------------------------------------------------ measurement */
+/* Integer throughput of the current GPU, measured: every SM busy with independent
+ * chains of 32-bit multiply-adds (*mad_ops_per_s, each counted as two operations)
+ * and of adds (*add_ops_per_s, one operation each), best of three timed runs of a
+ * few milliseconds on `stream` (cudaStream_t, NULL = legacy default stream;
+ * synchronises it). The denominator of the roofline of the integer-bound search
+ * kernels; the paper has no counterpart. Errors: QAP_ERR_INVALID_ARG,
+ * QAP_ERR_OOM, QAP_ERR_CUDA. */
+int qap_int32_peak(void* stream, double* mad_ops_per_s, double* add_ops_per_s);
+
 /* ------------------------------------------------ allocation-free statistics */
 /* The same statistics as pso_stats (min, 5/25/50/75 % nearest-rank percentiles,
  * max, mean), computed from `count` costs that the caller already holds in device
@@ -294,7 +341,9 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
  *
  * Scratch: one fixed device array inside this library (QAP_NOALLOC_MAX_COUNT
  * int64 sort slots plus 8 result slots, 512 KiB + 64 B), held by every GPU that
- * loads the library until the process exits. Each call rewrites every slot it
+ * loads the library until the process exits (placed when the driver loads the
+ * library's device code on that device; with CUDA's lazy module loading, at the
+ * first call there). Each call rewrites every slot it
  * reads, so nothing from an earlier call leaks into a result. All calls share
  * the one array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialized by the caller. The first call on a device

@@ -130,7 +130,8 @@ void orc_step(const orc_params* q, int n, const int32_t* F, const int32_t* D, ui
  * iteration t, given the post-local-search positions and costs of every particle. */
 void orc_bests_and_migration(const orc_params* q, int n, uint64_t seed, int t, orc_state* s);
 
-/* Nearest-rank percentiles of P costs: out = {min, p5, p25, p50, p75, max}, *mean. */
+/* Nearest-rank percentiles of P costs: out = {min, p5, p25, p50, p75, max}; *mean =
+ * the exact integer sum / P (quotient + remainder / P). */
 /* Histogram of costs: counts[0] below lo, counts[1 + b] for b = floor((cost - lo) bins /
  * (hi - lo)), counts[bins + 1] at or above hi (the PMF of section 4.2 times P). */
 void orc_histogram(const int64_t* cost, int P, int64_t lo, int64_t hi, int bins, int64_t* counts);

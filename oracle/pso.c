@@ -468,8 +468,11 @@ void orc_stats(const int64_t* cost, int P, int64_t out[6], double* mean) {
         out[1 + i] = v[rank - 1];
     }
     out[5] = v[P - 1];
-    double sum = 0.0;
-    for (int i = 0; i < P; ++i) sum += (double)v[i];
-    *mean = sum / P;
+    /* mean: the exact integer sum of the costs divided by P, as the quotient plus
+       remainder / P (the sum in 128 bits cannot overflow) */
+    __int128 sum = 0;
+    for (int i = 0; i < P; ++i) sum += v[i];
+    const __int128 quo = sum / P, rem = sum % P;
+    *mean = (double)(int64_t)quo + (double)(int64_t)rem / (double)P;
     free(v);
 }

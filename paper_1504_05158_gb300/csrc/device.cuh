@@ -56,6 +56,41 @@ __device__ __forceinline__ uint32_t below(uint32_t u, uint32_t k) {
     return (uint32_t)(((uint64_t)u * (uint64_t)k) >> 32);
 }
 
+// ------------------------------------------------ Eq. 4 at one cell, exactly
+// A product of two fp32 values held exactly as hi + lo (hi rounded, lo = the
+// rounding error, recovered by one fused multiply-add).
+struct Split {
+    float hi, lo;
+};
+__device__ __forceinline__ Split exact_mul(float x, float y) {
+    const float h = __fmul_rn(x, y);
+    return Split{h, __fmaf_rn(x, y, -h)};
+}
+// s = fl(x + y) and the rounding error x + y - s (Knuth's two-sum, six additions).
+__device__ __forceinline__ float two_sum(float x, float y, float& err) {
+    const float s = __fadd_rn(x, y);
+    const float bp = __fsub_rn(s, x);
+    err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(y, bp));
+    return s;
+}
+// c1 v + dl a + dg b for dl, dg in {-1, 0, 1} (the only values the differences of
+// permutation-matrix entries take in Eq. 4), with c1 v, a and b given as exact
+// splits: the hi parts are summed with error-free two-sums and every error term is
+// added back before the one final rounding (Ogita, Rump and Oishi's Sum2). The
+// result is the exact value rounded once, up to u^2 (u = 2^-24) of the terms, so it
+// keeps its relative accuracy when the terms cancel.
+__device__ __forceinline__ float eq4_cell(Split p, Split a, Split b, int dl, int dg) {
+    const float ah = dl == 0 ? 0.0f : (dl > 0 ? a.hi : -a.hi);
+    const float al = dl == 0 ? 0.0f : (dl > 0 ? a.lo : -a.lo);
+    const float bh = dg == 0 ? 0.0f : (dg > 0 ? b.hi : -b.hi);
+    const float bl = dg == 0 ? 0.0f : (dg > 0 ? b.lo : -b.lo);
+    float e1, e2;
+    const float s1 = two_sum(p.hi, ah, e1);
+    const float s2 = two_sum(s1, bh, e2);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p.lo, al), __fadd_rn(bl, e1)), e2);
+    return __fadd_rn(s2, lo);
+}
+
 // --------------------------------------------------------------- float keys
 // Monotone map float -> uint32 (larger float, larger key); +0 and -0 share a key;
 // no finite float maps to 0, which marks "nothing".

@@ -139,19 +139,28 @@ __global__ void __launch_bounds__(kThreads) k_bests(const StateView* __restrict_
 
 // ---------------------------------------------------------------- statistics
 // Nearest-rank percentiles of the current costs (section 4.2 reports 75/50/25/5 %
-// ranks): P_q = sorted[ceil(q N) - 1], from an in-CTA bitonic sort of a padded copy.
+// ranks): P_q = sorted[ceil(q N) - 1], from an in-CTA bitonic sort of a padded copy;
+// and the exact sum of the costs as a 128-bit integer (two int64 words), from which
+// the host forms the mean (no floating point on the device).
 __global__ void __launch_bounds__(kThreads) k_stats(const int64_t* cost, int count, int64_t* buf,
-                                                     int len, int64_t* out6, double* mean) {
-    __shared__ long long part[kThreads / 32];
-    long long sum = 0;
+                                                     int len, int64_t* out8) {
+    __shared__ long long part[kThreads / 32][2];
+    __int128 sum = 0;
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const long long c = i < count ? cost[i] : LLONG_MAX;
         buf[i] = c;
         if (i < count) sum += c;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long lo = __shfl_xor_sync(FULL, (long long)(unsigned long long)sum, o);
+        const long long hi = __shfl_xor_sync(FULL, (long long)(sum >> 64), o);
+        sum += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[threadIdx.x >> 5][0] = (long long)(unsigned long long)sum;
+        part[threadIdx.x >> 5][1] = (long long)(sum >> 64);
+    }
     __syncthreads();
     for (int k = 2; k <= len; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -170,16 +179,19 @@ __global__ void __launch_bounds__(kThreads) k_stats(const int64_t* cost, int cou
         }
     }
     if (threadIdx.x == 0) {
-        long long tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        __int128 tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            tot += (__int128)(((unsigned __int128)(unsigned long long)part[w][1] << 64) |
+                              (unsigned long long)part[w][0]);
         const int pct[4] = {5, 25, 50, 75};
-        out6[0] = buf[0];
+        out8[0] = buf[0];
         for (int q = 0; q < 4; ++q) {
             const long long rank = ((long long)pct[q] * count + 99) / 100;
-            out6[1 + q] = buf[rank - 1];
+            out8[1 + q] = buf[rank - 1];
         }
-        out6[5] = buf[count - 1];
-        *mean = (double)tot / (double)count;
+        out8[5] = buf[count - 1];
+        out8[6] = (long long)(unsigned long long)tot;
+        out8[7] = (long long)(tot >> 64);
     }
 }
 
@@ -201,10 +213,16 @@ cudaError_t launch_bests(const StateView* d_views, int count, int m_max, int ini
 }
 
 cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, int32_t scratch_len,
-                         int64_t* out6, double* mean, cudaStream_t st) {
+                         int64_t* out8, cudaStream_t st) {
     if (count < 1 || scratch_len < count || (scratch_len & (scratch_len - 1))) return cudaErrorInvalidValue;
-    k_stats<<<1, kThreads, 0, st>>>(cost, count, scratch, scratch_len, out6, mean);
+    k_stats<<<1, kThreads, 0, st>>>(cost, count, scratch, scratch_len, out8);
     return cudaGetLastError();
+}
+
+double mean_of_sum(int64_t sum_lo, int64_t sum_hi, int32_t count) {
+    const __int128 sum = (__int128)(((unsigned __int128)(uint64_t)sum_hi << 64) | (uint64_t)sum_lo);
+    const __int128 q = sum / count, r = sum % count;  // truncated: r has the sign of sum
+    return (double)(int64_t)q + (double)(int64_t)r / (double)count;
 }
 
 }  // namespace qap

@@ -25,8 +25,6 @@
 // shared memory; each warp owns one particle's G (n rows of n+1 int32, the odd
 // stride keeps column gathers free of bank conflicts), G[k][p(k)] and p.
 #include <climits>
-#include <cstdlib>
-#include <cstring>
 
 #include <cuda_fp16.h>
 
@@ -44,12 +42,23 @@ constexpr size_t kSmemLimit = 227 * 1024;
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t shared_part(int n) {
-    return align16((size_t)n * round_up(n, 4) * 4) + align16((size_t)n * n * 2);
+// Shared memory of the SIMT searches. GT is the integer type of the table G (int32
+// when every swap value fits, int64 otherwise), DT the staged type of D (uint16 or
+// int32). F (int32, rows padded to fs = n rounded up to 4) and D are staged in
+// shared memory when they fit beside the warps' tables, else read from global
+// memory through the cache (fs = n); per warp: G (n rows of n + 1), G[k][p(k)], p.
+template <typename GT, typename DT>
+__host__ __device__ inline size_t simt_fd_bytes(int n) {
+    return align16((size_t)n * round_up(n, 4) * 4) + align16((size_t)n * n * sizeof(DT));
 }
-__host__ __device__ inline size_t g_bytes(int n) { return align16((size_t)n * (n + 1) * 4); }
-__host__ __device__ inline size_t warp_part(int n) {
-    return g_bytes(n) + align16((size_t)n * 4) * 2;
+template <typename GT>
+__host__ __device__ inline size_t simt_warp_bytes(int n) {
+    return align16((size_t)n * (n + 1) * sizeof(GT)) + align16((size_t)n * sizeof(GT)) + align16((size_t)n * 4);
+}
+// F and D go to shared memory when they fit beside `wpc` warps in `smem` bytes
+template <typename GT, typename DT>
+__host__ __device__ inline bool simt_staged(int n, int wpc, size_t smem) {
+    return simt_fd_bytes<GT, DT>(n) + (size_t)wpc * simt_warp_bytes<GT>(n) <= smem;
 }
 
 __device__ __forceinline__ long long warp_sum64(long long v) {
@@ -58,29 +67,44 @@ __device__ __forceinline__ long long warp_sum64(long long v) {
     return v;
 }
 
-// Stages F (int32, rows padded to fs) and D (uint16) for the searches.
-__device__ __forceinline__ void stage_fd(const LsArgs& a, int32_t* sF, uint16_t* sD, int fs) {
-    const int n = a.n;
-    for (int i = threadIdx.x; i < n * fs; i += blockDim.x) {
-        const int r = i / fs, c = i % fs;
-        sF[i] = c < n ? a.F[r * n + c] : 0;
+// warp-wide lexicographic minimum of (value, key)
+template <typename GT>
+__device__ __forceinline__ void warp_min2(GT& v, unsigned& key) {
+    if constexpr (sizeof(GT) == 4) {
+        const int mv = __reduce_min_sync(FULL, (int)v);
+        key = __reduce_min_sync(FULL, (int)v == mv ? key : 0xFFFFFFFFu);
+        v = (GT)mv;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const GT ov = __shfl_xor_sync(FULL, v, o);
+            const unsigned ok = __shfl_xor_sync(FULL, key, o);
+            if (ov < v || (ov == v && ok < key)) {
+                v = ov;
+                key = ok;
+            }
+        }
     }
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = (uint16_t)a.D[i];
+}
+
+template <typename GT>
+__device__ __forceinline__ GT gt_max() {
+    return sizeof(GT) == 4 ? (GT)INT_MAX : (GT)LLONG_MAX;
 }
 
 // Best-improvement descent of particle p from a complete G (rounds of all pairs,
-// rank-1 updates), then its outputs: position, cost, counters, local best.
-template <int NW>
-__device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const int32_t* sF,
-                                                  const uint16_t* sD, int32_t* G, int32_t* gd,
-                                                  int32_t* pi, int lane) {
-    const int n = a.n, fs = round_up(n, 4), gs = n + 1;
+// rank-1 updates), then its outputs: position, cost, counters, local best. F has
+// row stride fs; Dm is D (n x n) in shared or global memory.
+template <int NW, typename GT, typename DT>
+__device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const int32_t* F, int fs,
+                                                  const DT* Dm, GT* G, GT* gd, int32_t* pi, int lane) {
+    const int n = a.n, gs = n + 1;
     const long long npairs = (long long)n * (n - 1) / 2;
     const int nv = n / 2;  // virtual rows: row t joined with row n-2-t
     long long part = 0;
     for (int m = lane; m < n; m += 32) {
         gd[m] = G[m * gs + pi[m]];
-        part += gd[m];
+        part += (long long)gd[m];
     }
     long long cost = warp_sum64(part);
     __syncwarp();
@@ -91,7 +115,7 @@ __device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const 
             if (lane == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
             break;
         }
-        int best = INT_MAX;
+        GT best = gt_max<GT>();
         unsigned bkey = 0xFFFFFFFFu;
         for (int t = 0; t < nv; ++t) {
 #pragma unroll
@@ -108,8 +132,8 @@ __device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const 
                     if (k == t) continue;
                 }
                 const int pk = pi[k], pmm = pi[m];
-                const int d = 2 * (G[k * gs + pmm] + G[m * gs + pk] - gd[k] - gd[m]) +
-                              4 * sF[k * fs + m] * (int)sD[pk * n + pmm];
+                const GT d = 2 * (G[k * gs + pmm] + G[m * gs + pk] - gd[k] - gd[m]) +
+                             4 * (GT)F[k * fs + m] * (GT)Dm[pk * n + pmm];
                 const unsigned key = ((unsigned)k << 8) | (unsigned)m;
                 if (d < best || (d == best && key < bkey)) {
                     best = d;
@@ -118,23 +142,22 @@ __device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const 
             }
         }
         ++rounds;
-        const int mn = __reduce_min_sync(FULL, best);
-        const unsigned kmin = __reduce_min_sync(FULL, best == mn ? bkey : 0xFFFFFFFFu);
-        if (mn >= 0) break;
-        const int r = (int)(kmin >> 8), s = (int)(kmin & 255u);
+        warp_min2<GT>(best, bkey);
+        if (best >= 0) break;
+        const int r = (int)(bkey >> 8), s = (int)(bkey & 255u);
         if (r >= n || s >= n || r >= s) {  // cannot happen; never index with it
             if (lane == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
             break;
         }
         const int pr = pi[r], pss = pi[s];
-        int bt[NW];
+        GT bt[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int l = lane + 32 * w;
-            bt[w] = l < n ? (int)sD[pss * n + l] - (int)sD[pr * n + l] : 0;
+            bt[w] = l < n ? (GT)((long long)Dm[pss * n + l] - (long long)Dm[pr * n + l]) : (GT)0;
         }
         for (int k = 0; k < n; ++k) {
-            const int ak = sF[r * fs + k] - sF[s * fs + k];
+            const GT ak = (GT)((long long)F[r * fs + k] - (long long)F[s * fs + k]);
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 const int l = lane + 32 * w;
@@ -149,7 +172,7 @@ __device__ __forceinline__ void descend_and_store(const LsArgs& a, int p, const 
         __syncwarp();
         for (int m = lane; m < n; m += 32) gd[m] = G[m * gs + pi[m]];
         __syncwarp();
-        cost += mn;
+        cost += (long long)best;
         ++moves;
     }
     for (int m = lane; m < n; m += 32) a.out[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
@@ -198,37 +221,66 @@ __device__ __forceinline__ void store_cost_only(const LsArgs& a, int p, long lon
     __syncwarp();
 }
 
+// the next particle of warp-per-particle kernels: from the population's counter,
+// else a fixed stride
+__device__ __forceinline__ int next_particle(const LsArgs& a, int& p, int stride, int lane) {
+    if (a.work) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(a.work, 1);
+        return __shfl_sync(FULL, q, 0);
+    }
+    const int cur = p;
+    p += stride;
+    return cur;
+}
+
 // ------------------------------------------------------------ SIMT set-up
-// cpi CTAs per population of the table: CTA b serves population b / cpi
-template <int NW>
-__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __restrict__ args, int cpi,
-                                                             int wpc) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+// G = F * D_p by integer multiply-adds, one warp per particle; cpi CTAs per
+// population of the table (CTA b serves population b / cpi), wpc warps per CTA,
+// `smem` bytes of dynamic shared memory (sized for the largest n of the table).
+// GT = int32 when every value of G and every swap value fits (n max_f max_d <
+// 2^27) and D fits 16 bits (DT = uint16); else GT = int64 with DT = int32 (exact
+// while (n^2 + 8 n + 4) max_f max_d < 2^62).
+template <int NW, typename GT, typename DT>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __restrict__ args, int cpi, int wpc,
+                                                             int smem) {
+    extern __shared__ __align__(1024) unsigned char smem_buf[];
     const LsArgs a = args[blockIdx.x / cpi];
     const int cb = blockIdx.x % cpi;
-    const int n = a.n, fs = round_up(n, 4), gs = n + 1;
+    const int n = a.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t* sF = reinterpret_cast<int32_t*>(smem);
-    uint16_t* sD = reinterpret_cast<uint16_t*>(smem + align16((size_t)n * fs * 4));
-    unsigned char* wb = smem + shared_part(n) + (size_t)warp * warp_part(n);
-    int32_t* G = reinterpret_cast<int32_t*>(wb);
-    int32_t* gd = reinterpret_cast<int32_t*>(wb + g_bytes(n));
-    int32_t* pi = gd + align16((size_t)n * 4) / 4;
-
-    stage_fd(a, sF, sD, fs);
-    __syncthreads();
-    if (warp >= wpc) return;
-
-    int p = cb * wpc + warp;
-    for (;;) {
-        if (a.work) {
-            int q = 0;
-            if (lane == 0) q = atomicAdd(a.work, 1);
-            p = __shfl_sync(FULL, q, 0);
+    const bool staged = simt_staged<GT, DT>(n, wpc, (size_t)smem);
+    const int fs = staged ? round_up(n, 4) : n;
+    const int32_t* F = a.F;
+    const DT* Dm = nullptr;
+    unsigned char* wb0 = smem_buf;
+    if (staged) {
+        int32_t* sF = reinterpret_cast<int32_t*>(smem_buf);
+        DT* sD = reinterpret_cast<DT*>(smem_buf + align16((size_t)n * fs * 4));
+        for (int i = threadIdx.x; i < n * fs; i += blockDim.x) {
+            const int r = i / fs, c = i % fs;
+            sF[i] = c < n ? a.F[r * n + c] : 0;
         }
-        if (p >= a.count) break;
-        const int pcur = p;
-        if (!a.work) p += cpi * wpc;
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = (DT)a.D[i];
+        F = sF;
+        Dm = sD;
+        wb0 += simt_fd_bytes<GT, DT>(n);
+    } else {
+        if constexpr (sizeof(DT) == 4) Dm = reinterpret_cast<const DT*>(a.D);
+    }
+    __syncthreads();
+    if (warp >= wpc || !Dm) return;  // (the launcher stages 16-bit D always)
+    unsigned char* wb = wb0 + (size_t)warp * simt_warp_bytes<GT>(n);
+    GT* G = reinterpret_cast<GT*>(wb);
+    GT* gd = reinterpret_cast<GT*>(wb + align16((size_t)n * (n + 1) * sizeof(GT)));
+    int32_t* pi = reinterpret_cast<int32_t*>(wb + align16((size_t)n * (n + 1) * sizeof(GT)) +
+                                             align16((size_t)n * sizeof(GT)));
+    const int gs = n + 1;
+
+    int pnext = cb * wpc + warp;
+    for (;;) {
+        const int pcur = next_particle(a, pnext, cpi * wpc, lane);
+        if (pcur >= a.count) break;
         for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)pcur * a.ps_in + m];
         __syncwarp();
         int pm[NW];
@@ -245,7 +297,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
                 const int j = lane + 32 * w;
                 if (j < n) {
                     long long col = 0;
-                    for (int i = 0; i < n; ++i) col += (long long)sF[i * fs + j] * (int)sD[pi[i] * n + pm[w]];
+                    for (int i = 0; i < n; ++i) col += (long long)F[i * fs + j] * (long long)Dm[pi[i] * n + pm[w]];
                     part += col;
                 }
             }
@@ -253,33 +305,42 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
             continue;
         }
         // ---- set-up: G = F * D_p (rows of D gathered by p) ----
-        constexpr int KC = NW <= 2 ? 32 : 16;
+        constexpr int KC = sizeof(GT) == 8 ? 8 : (NW <= 2 ? 32 : 16);
         for (int kc = 0; kc < n; kc += KC) {
-            int acc[KC][NW];
+            GT acc[KC][NW];
 #pragma unroll
             for (int kk = 0; kk < KC; ++kk)
 #pragma unroll
                 for (int w = 0; w < NW; ++w) acc[kk][w] = 0;
             for (int j = 0; j < n; ++j) {
                 const int pj = pi[j];
-                int dv[NW];
+                GT dv[NW];
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
                     const int l = lane + 32 * w;
-                    dv[w] = l < n ? (int)sD[pj * n + l] : 0;
+                    dv[w] = l < n ? (GT)Dm[pj * n + l] : (GT)0;
                 }
                 // F[k][j] = F[j][k] (symmetric): a contiguous, broadcast row slice
-                const int32_t* frow = sF + j * fs + kc;
+                const int32_t* frow = F + j * fs + kc;
+                if (staged) {
 #pragma unroll
-                for (int q = 0; q < KC / 4; ++q) {
-                    int4 f4 = make_int4(0, 0, 0, 0);
-                    if (kc + 4 * q < fs) f4 = *reinterpret_cast<const int4*>(frow + 4 * q);
+                    for (int q = 0; q < KC / 4; ++q) {
+                        int4 f4 = make_int4(0, 0, 0, 0);
+                        if (kc + 4 * q < fs) f4 = *reinterpret_cast<const int4*>(frow + 4 * q);
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        acc[4 * q + 0][w] += f4.x * dv[w];
-                        acc[4 * q + 1][w] += f4.y * dv[w];
-                        acc[4 * q + 2][w] += f4.z * dv[w];
-                        acc[4 * q + 3][w] += f4.w * dv[w];
+                        for (int w = 0; w < NW; ++w) {
+                            acc[4 * q + 0][w] += (GT)f4.x * dv[w];
+                            acc[4 * q + 1][w] += (GT)f4.y * dv[w];
+                            acc[4 * q + 2][w] += (GT)f4.z * dv[w];
+                            acc[4 * q + 3][w] += (GT)f4.w * dv[w];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < KC; ++q) {
+                        const GT f = kc + q < n ? (GT)__ldg(frow + q) : (GT)0;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) acc[q][w] += f * dv[w];
                     }
                 }
             }
@@ -295,7 +356,130 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
             }
         }
         __syncwarp();
-        descend_and_store<NW>(a, pcur, sF, sD, G, gd, pi, lane);
+        descend_and_store<NW, GT, DT>(a, pcur, F, fs, Dm, G, gd, pi, lane);
+    }
+}
+
+// ------------------------------------------------- direct search (any instance)
+// The goal function and the swap search for any F and D (not symmetric, nonzero
+// diagonal, entries up to 2^31 - 1) in exact int64 arithmetic: every round takes
+// each pair's value from the general O(n) formula (the terms of the double sum whose
+// row or column index is r or s), so nothing but p is kept per particle. One warp per
+// particle; F and D (int32) in shared memory when they fit, else read through the
+// cache. Exact while (n^2 + 8 n + 4) max_f max_d < 2^62.
+__device__ __forceinline__ long long delta_general(const int32_t* F, const int32_t* D, const int32_t* pi, int n,
+                                                   int r, int s) {
+    const int pr = pi[r], ps = pi[s];
+    long long d = (long long)(F[r * n + r] - F[s * n + s]) * (long long)(D[ps * n + ps] - D[pr * n + pr]) +
+                  (long long)(F[r * n + s] - F[s * n + r]) * (long long)(D[ps * n + pr] - D[pr * n + ps]);
+    for (int k = 0; k < n; ++k) {
+        if (k == r || k == s) continue;
+        const int pk = pi[k];
+        d += (long long)(F[k * n + r] - F[k * n + s]) * (long long)(D[pk * n + ps] - D[pk * n + pr]);
+        d += (long long)(F[r * n + k] - F[s * n + k]) * (long long)(D[ps * n + pk] - D[pr * n + pk]);
+    }
+    return d;
+}
+
+__host__ __device__ inline size_t direct_fd_bytes(int n) { return 2 * align16((size_t)n * n * 4); }
+__host__ __device__ inline size_t direct_warp_bytes(int n) { return align16((size_t)n * 4); }
+
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls_direct(const LsArgs* __restrict__ args, int cpi,
+                                                                    int wpc, int smem) {
+    extern __shared__ __align__(1024) unsigned char smem_buf[];
+    const LsArgs a = args[blockIdx.x / cpi];
+    const int cb = blockIdx.x % cpi;
+    const int n = a.n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool staged = direct_fd_bytes(n) + (size_t)wpc * direct_warp_bytes(n) <= (size_t)smem;
+    const int32_t* F = a.F;
+    const int32_t* D = a.D;
+    unsigned char* wb0 = smem_buf;
+    if (staged) {
+        int32_t* sF = reinterpret_cast<int32_t*>(smem_buf);
+        int32_t* sD = reinterpret_cast<int32_t*>(smem_buf + align16((size_t)n * n * 4));
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+            sF[i] = a.F[i];
+            sD[i] = a.D[i];
+        }
+        F = sF;
+        D = sD;
+        wb0 += direct_fd_bytes(n);
+    }
+    __syncthreads();
+    if (warp >= wpc) return;
+    int32_t* pi = reinterpret_cast<int32_t*>(wb0 + (size_t)warp * direct_warp_bytes(n));
+    const long long npairs = (long long)n * (n - 1) / 2;
+    int pnext = cb * wpc + warp;
+    for (;;) {
+        const int p = next_particle(a, pnext, cpi * wpc, lane);
+        if (p >= a.count) break;
+        for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)p * a.ps_in + m];
+        __syncwarp();
+        long long part = 0;
+        for (int i = lane; i < n; i += 32)
+            for (int j = 0; j < n; ++j) part += (long long)F[i * n + j] * (long long)D[pi[i] * n + pi[j]];
+        long long cost = warp_sum64(part);
+        if (a.max_moves < 0) {
+            store_cost_only(a, p, cost, pi, lane);
+            continue;
+        }
+        int moves = 0, rounds = 0;
+        for (;;) {
+            if (a.max_moves > 0 && moves >= a.max_moves) break;
+            if (moves >= kSafetyMoves) {
+                if (lane == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            long long best = LLONG_MAX;
+            unsigned bkey = 0xFFFFFFFFu;
+            for (int r = 0; r < n - 1; ++r)
+                for (int s = r + 1 + lane; s < n; s += 32) {
+                    const long long d = delta_general(F, D, pi, n, r, s);
+                    const unsigned key = ((unsigned)r << 8) | (unsigned)s;
+                    if (d < best || (d == best && key < bkey)) {
+                        best = d;
+                        bkey = key;
+                    }
+                }
+            ++rounds;
+            warp_min2<long long>(best, bkey);
+            if (best >= 0) break;
+            const int r = (int)(bkey >> 8), s = (int)(bkey & 255u);
+            if (r >= n || s >= n || r >= s) {  // cannot happen; never index with it
+                if (lane == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const int t = pi[r];
+                pi[r] = pi[s];
+                pi[s] = t;
+            }
+            __syncwarp();
+            cost += best;
+            ++moves;
+        }
+        for (int m = lane; m < n; m += 32) a.out[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+        if (a.PL) {
+            const long long old = a.costL[p];
+            if (cost < old) {
+                for (int m = lane; m < n; m += 32) a.PL[(size_t)p * a.ps_out + m] = (uint8_t)pi[m];
+                if (lane == 0) a.costL[p] = cost;
+            }
+        }
+        if (lane == 0) {
+            a.cost[p] = cost;
+            if (a.moves) a.moves[p] = moves;
+            if (a.rounds) a.rounds[p] = rounds;
+            if (a.counters) {
+                atomicAdd(a.counters + CNT_PIT, 1ull);
+                atomicAdd(a.counters + CNT_MOVES, (unsigned long long)moves);
+                atomicAdd(a.counters + CNT_ROUNDS, (unsigned long long)rounds);
+                atomicAdd(a.counters + CNT_DELTA_FULL, (unsigned long long)(rounds * npairs));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -804,11 +988,14 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
             tc::mma_commit(bar);
         }
         const bool ok = team_all<WPP>(mbar_wait(bar, phase), team);
-        phase ^= 1u;
-        if (!ok) {  // the product never completed: record and leave (cannot be expected)
-            if (tt == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+        if (!ok) {  // the product did not complete in time: record and leave
+            if (tt == 0) {
+                if (a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                mbar_wait(bar, phase);  // one more bounded wait before the tensor memory is freed
+            }
             break;
         }
+        phase ^= 1u;
         tc::fence_after_sync();
         // G_p from tensor memory, written as H + F o Dp (it overwrites the B tile,
         // which the completed product no longer reads): reader warp w holds rows
@@ -916,17 +1103,14 @@ cudaError_t launch_team(const LsLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int NW>
-cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
-    const int n = L.n_max;
-    int wpc = kMaxWarpsPerCta;
-    while (wpc > 1 && shared_part(n) + wpc * warp_part(n) > kSmemLimit) --wpc;
-    const size_t smem = shared_part(n) + wpc * warp_part(n);
+// one launch of a warp-per-particle search kernel K with wpc warps and smem bytes
+template <auto K>
+cudaError_t launch_warp_kernel(const LsLaunch& L, int wpc, size_t smem, cudaStream_t st) {
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = configure_once<k_ls<NW>>();
+    cudaError_t e = configure_once<K>();
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
-    int per_sm = occupancy_cached<k_ls<NW>>(wpc * 32, smem);
+    int per_sm = occupancy_cached<K>(wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int cpi = L.cpi;
     if (cpi <= 0) {
@@ -937,8 +1121,58 @@ cudaError_t launch_nw(const LsLaunch& L, cudaStream_t st) {
     }
     e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t) * L.count, st);
     if (e != cudaSuccess) return e;
-    k_ls<NW><<<L.count * cpi, wpc * 32, smem, st>>>(L.d_args, cpi, wpc);
+    K<<<L.count * cpi, wpc * 32, smem, st>>>(L.d_args, cpi, wpc, (int)smem);
     return cudaGetLastError();
+}
+
+// largest n whose SIMT search fits one warp in shared memory (with F and D staged
+// when D has 16 bits: that variant always stages them)
+template <typename GT, typename DT>
+int simt_max_n() {
+    int n = 2;
+    while (n < 256) {
+        const int m = n + 1;
+        const size_t need = simt_warp_bytes<GT>(m) + (sizeof(DT) == 2 ? simt_fd_bytes<GT, DT>(m) : 0);
+        if (need > kSmemLimit) break;
+        n = m;
+    }
+    return n;
+}
+
+template <int NW, typename GT, typename DT>
+cudaError_t launch_simt(const LsLaunch& L, cudaStream_t st) {
+    const int n = L.n_max;
+    const size_t fd = simt_fd_bytes<GT, DT>(n), pw = simt_warp_bytes<GT>(n);
+    int w_staged = kMaxWarpsPerCta;
+    while (w_staged > 0 && fd + w_staged * pw > kSmemLimit) --w_staged;
+    int w_global = kMaxWarpsPerCta;
+    while (w_global > 0 && w_global * pw > kSmemLimit) --w_global;
+    // 16-bit D is always staged; 32-bit F and D are staged unless that halves the warps
+    const bool staged = sizeof(DT) == 2 ? true : (w_staged >= 1 && 2 * w_staged >= w_global);
+    const int wpc = staged ? w_staged : w_global;
+    if (wpc < 1) return cudaErrorInvalidValue;
+    return launch_warp_kernel<k_ls<NW, GT, DT>>(L, wpc, (staged ? fd : 0) + wpc * pw, st);
+}
+
+cudaError_t launch_direct(const LsLaunch& L, cudaStream_t st) {
+    const int n = L.n_max;
+    const int wpc = kMaxWarpsPerCta;
+    const size_t fd = direct_fd_bytes(n), pw = direct_warp_bytes(n);
+    const bool staged = fd + wpc * pw <= kSmemLimit;
+    return launch_warp_kernel<k_ls_direct>(L, wpc, (staged ? fd : 0) + wpc * pw, st);
+}
+
+template <typename GT, typename DT>
+cudaError_t launch_simt_t(const LsLaunch& L, cudaStream_t st) {
+    switch ((L.n_max + 31) / 32) {
+        case 1: return launch_simt<1, GT, DT>(L, st);
+        case 2: return launch_simt<2, GT, DT>(L, st);
+        case 3: return launch_simt<3, GT, DT>(L, st);
+        case 4: return launch_simt<4, GT, DT>(L, st);
+        case 5: return launch_simt<5, GT, DT>(L, st);
+        case 6: return launch_simt<6, GT, DT>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------ general instances (any F, D)
@@ -1256,11 +1490,14 @@ __global__ void __launch_bounds__(256, 2) k_ls_gen(const LsArgs* __restrict__ ar
             tc::mma_commit(bar);
         }
         const bool ok = team_all<8>(mbar_wait(bar, phase), 0);
-        phase ^= 1u;
-        if (!ok) {
-            if (tid == 0 && a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+        if (!ok) {  // the product did not complete in time: record and leave
+            if (tid == 0) {
+                if (a.counters) atomicAdd(a.counters + CNT_ERR, 1ull);
+                mbar_wait(bar, phase);  // one more bounded wait before the tensor memory is freed
+            }
             break;
         }
+        phase ^= 1u;
         tc::fence_after_sync();
         if (warp < 4) {  // rows k = 32 warp + lane, lane quarter = warp
             const int k = 32 * warp + lane;
@@ -1329,40 +1566,64 @@ cudaError_t launch_gen(const LsLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-int ls_max_n(int tc_flags) {
-    int n = 2;  // the SIMT kernel: one warp's G and the staged F, D in shared memory
-    while (n < 256 && shared_part(n + 1) + warp_part(n + 1) <= kSmemLimit) ++n;
-    if (n > 160) n = 160;
-    if ((tc_flags & 3) == 3 && n < 160) n = 160;  // the 8-bit tensor-core search
-    return n;
+int ls_max_n(LsKind kind) {
+    switch (kind) {
+        case LS_TEAM1: return 32;
+        case LS_TEAM2: return 64;
+        case LS_TEAM8: return 128;
+        case LS_TEAM8N: return 160;
+        case LS_GEN: return 128;
+        case LS_SIMT: return simt_max_n<int32_t, uint16_t>();
+        case LS_SIMT64: return simt_max_n<int64_t, int32_t>();
+        case LS_DIRECT: return 256;
+        default: return 0;
+    }
 }
 
 LsKind ls_kind(const LsArgs& a) {
-    const char* env = getenv("QAP_PSO_LS_SETUP");
-    const bool simt = env && strcmp(env, "simt") == 0;
-    if (!(a.tc_exact & 1)) return (a.tc_exact & 4) && a.n <= 128 ? LS_GEN : LS_SIMT;
-    if (simt && a.n <= ls_max_n(0)) return LS_SIMT;
-    if (a.n <= 32) return LS_TEAM1;
-    if (a.n <= 64) return LS_TEAM2;
-    if (a.n <= 128) return LS_TEAM8;
-    // past 128 rows only the 8-bit staging of F and Dp (entries <= 255) fits shared memory
-    return (a.tc_exact & 2) && a.n <= 160 ? LS_TEAM8N : LS_SIMT;
+    if (a.force >= 0) return (LsKind)a.force;
+    const int n = a.n;
+    if (!a.sym) return (a.tc_exact & 4) && n <= ls_max_n(LS_GEN) ? LS_GEN : LS_DIRECT;
+    if (a.tc_exact & 1) {
+        if (n <= 32) return LS_TEAM1;
+        if (n <= 64) return LS_TEAM2;
+        if (n <= 128) return LS_TEAM8;
+        // past 128 rows only the 8-bit staging of F and Dp (entries <= 255) fits shared memory
+        if ((a.tc_exact & 2) && n <= 160) return LS_TEAM8N;
+    }
+    if (a.exact32 && n <= ls_max_n(LS_SIMT)) return LS_SIMT;
+    if (n <= ls_max_n(LS_SIMT64)) return LS_SIMT64;
+    return LS_DIRECT;
+}
+
+bool ls_kind_serves(LsKind kind, const LsArgs& a) {
+    const int n = a.n;
+    if (n < 2 || n > ls_max_n(kind)) return false;
+    switch (kind) {
+        case LS_TEAM1:
+        case LS_TEAM2:
+        case LS_TEAM8: return (a.tc_exact & 1) != 0;
+        case LS_TEAM8N: return (a.tc_exact & 3) == 3 && n > 128;
+        case LS_GEN: return (a.tc_exact & 4) != 0;
+        case LS_SIMT: return a.sym && a.exact32;
+        case LS_SIMT64: return a.sym != 0;
+        case LS_DIRECT: return true;
+        default: return false;
+    }
 }
 
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st) {
     if (L.count <= 0 || L.total <= 0) return cudaSuccess;
-    if (L.n_max < 2 || L.n_max > ls_max_n(L.kind == LS_TEAM8N ? 3 : 0)) return cudaErrorInvalidValue;
-    if (L.kind == LS_TEAM1) return launch_team<1, uint16_t>(L, st);
-    if (L.kind == LS_TEAM2) return launch_team<2, uint16_t>(L, st);
-    if (L.kind == LS_TEAM8) return launch_team<8, uint16_t>(L, st);
-    if (L.kind == LS_TEAM8N) return launch_team<8, uint8_t>(L, st);
-    if (L.kind == LS_GEN) return launch_gen(L, st);
-    switch ((L.n_max + 31) / 32) {
-        case 1: return launch_nw<1>(L, st);
-        case 2: return launch_nw<2>(L, st);
-        case 3: return launch_nw<3>(L, st);
-        case 4: return launch_nw<4>(L, st);
-        case 5: return launch_nw<5>(L, st);
+    if (L.n_max < 2 || L.n_max > ls_max_n((LsKind)L.kind)) return cudaErrorInvalidValue;
+    switch (L.kind) {
+        case LS_TEAM1: return launch_team<1, uint16_t>(L, st);
+        case LS_TEAM2: return launch_team<2, uint16_t>(L, st);
+        case LS_TEAM8: return launch_team<8, uint16_t>(L, st);
+        case LS_TEAM8N: return launch_team<8, uint8_t>(L, st);
+        case LS_GEN: return launch_gen(L, st);
+        case LS_SIMT: return launch_simt_t<int32_t, uint16_t>(L, st);
+        case LS_SIMT64: return launch_simt_t<int64_t, int32_t>(L, st);
+        case LS_DIRECT: return launch_direct(L, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(kVelWarps * 32)
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ float part[kVelWarps][32 * NW];
     __shared__ float inv_s[32 * NW];
-    __shared__ float ab_s[2][2];  // c2 r2 and c3 r3 of the particle of each buffer
+    __shared__ Split ab_s[2][2];  // c2 r2 and c3 r3 (exact splits) of the particle of each buffer
     __shared__ __align__(8) uint64_t bar[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const size_t tb_max = tile_bytes<VT>(n_max);
@@ -785,23 +785,27 @@ __global__ void __launch_bounds__(kVelWarps * 32)
         }
         if (tid == 0) {  // one draw per particle, shared through shared memory
             const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-            ab_s[slot][0] = s.c2 * u01f(ur.x);
-            ab_s[slot][1] = s.c3 * u01f(ur.y);
+            ab_s[slot][0] = exact_mul(s.c2, u01f(ur.x));
+            ab_s[slot][1] = exact_mul(s.c3, u01f(ur.y));
         }
         const bool norm = s.sv_kind == 1;
         // one warp waits for the tile; the CTA barrier passes it on (and orders every
         // warp's reads of the other buffer, from the previous particle, before its refill)
         bool landed = true;
-        if (warp == 0) landed = mbar_wait(bar + slot, slot ? par1 : par0);
+        const uint32_t par = slot ? par1 : par0;
+        if (warp == 0) landed = mbar_wait(bar + slot, par);
         const bool ok = __syncthreads_and(landed);
-        const float a = ab_s[slot][0], b = ab_s[slot][1];
+        const Split a = ab_s[slot][0], b = ab_s[slot][1];
         if (slot)
             par1 ^= 1u;
         else
             par0 ^= 1u;
-        if (!ok) {  // the copy never landed: record, stop this CTA
+        if (!ok) {  // the copy did not land in time: record, stop this CTA
             if (tid == 0) {
                 atomicAdd(s.counters + CNT_ERR, 1ull);
+                // the load may still be in flight into this CTA's shared memory: give it
+                // one more bounded wait before the CTA exits, and let the stores finish
+                mbar_wait(bar + slot, par);
                 bulk_wait_all();
             }
             return;
@@ -819,14 +823,15 @@ __global__ void __launch_bounds__(kVelWarps * 32)
         }
         VT* tile = reinterpret_cast<VT*>(smem + (size_t)slot * tb_max);
         // W at a cell: c1 v + a dl + b dg, clamped; dl and dg vanish outside the rows
-        // X(t), P^L and P^G of the column, where W is clamp(c1 v) (the same fp32 value:
-        // fmaf(c1, v, 0) rounds like c1 * v)
-        auto wgen = [&](float v) { return fminf(fmaxf(s.c1 * v, -s.v_max), s.v_max); };
+        // X(t), P^L and P^G of the column, where W is clamp(c1 v). At those rows the
+        // terms can cancel, so W is formed from exact splits and rounded once (eq4_cell);
+        // with dl = dg = 0 that gives the same fp32 value as c1 v
+        auto wgen = [&](float v) { return fminf(fmaxf(__fmul_rn(s.c1, v), -s.v_max), s.v_max); };
         auto wval = [&](int i, int c) {
             const float v = VStore<VT>::to_f(tile[i * n + lane + 32 * c]);
-            const float dl = (float)((plc[c] == i) - (pic[c] == i));
-            const float dg = (float)((pgc[c] == i) - (pic[c] == i));
-            return fminf(fmaxf(fmaf(s.c1, v, a * dl + b * dg), -s.v_max), s.v_max);
+            const int dl = (plc[c] == i) - (pic[c] == i);
+            const int dg = (pgc[c] == i) - (pic[c] == i);
+            return fminf(fmaxf(eq4_cell(exact_mul(s.c1, v), a, b, dl, dg), -s.v_max), s.v_max);
         };
         // the distinct special rows of column c owned by this warp: row i of the tile
         // belongs to warp i mod kVelWarps
@@ -940,12 +945,13 @@ __global__ void __launch_bounds__(128)
             pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
         }
         const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-        const float a = s.c2 * u01f(ur.x), b = s.c3 * u01f(ur.y);
+        const Split a = exact_mul(s.c2, u01f(ur.x)), b = exact_mul(s.c3, u01f(ur.y));
         const bool norm = s.sv_kind == 1;
         auto wval = [&](int i, int c, float x0) {
-            const float dl = (float)((plc[c] == i) - (pic[c] == i));
-            const float dg = (float)((pgc[c] == i) - (pic[c] == i));
-            return fminf(fmaxf(fmaf(s.c1, x0, a * dl + b * dg), -s.v_max), s.v_max);
+            const int dl = (plc[c] == i) - (pic[c] == i);
+            const int dg = (pgc[c] == i) - (pic[c] == i);
+            const float w = (dl | dg) ? eq4_cell(exact_mul(s.c1, x0), a, b, dl, dg) : __fmul_rn(s.c1, x0);
+            return fminf(fmaxf(w, -s.v_max), s.v_max);
         };
         float inv[NW];
 #pragma unroll
@@ -1049,11 +1055,14 @@ __global__ void __launch_bounds__(kWarps * 32)
             newp[w] = 0;
         }
         const bool ok = mbar_wait(bar, phase);
-        phase ^= 1u;
-        if (!__all_sync(FULL, ok)) {  // the copy never landed: record, leave this warp
-            if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+        if (!__all_sync(FULL, ok)) {  // the copy did not land in time: record, leave this warp
+            if (lane == 0) {
+                atomicAdd(s.counters + CNT_ERR, 1ull);
+                mbar_wait(bar, phase);  // one more bounded wait for a load still in flight
+            }
             return;
         }
+        phase ^= 1u;
         // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
         // the discretisation entry point
         const float zadd = sx_only ? 0.0f : 1.0f;

@@ -29,7 +29,7 @@ struct LsArgs {
     unsigned long long* counters;  // may be null
     int32_t max_moves; // < 0: goal function only; 0: to a local optimum; > 0: cap
     int32_t tc_exact;  // bit 0: symmetric, zero diagonal, entries <= 2048 and n max_f max_d < 2^24:
-                       // the tensor-core set-up is exact (QAP_PSO_LS_SETUP=simt forces SIMT);
+                       // the tensor-core set-up is exact;
                        // bit 1: also every entry <= 255 (8-bit staging of F and D);
                        // bit 2: any F, D (not symmetric or not zero-diagonal) with entries
                        // <= 2048, 2 n max_f max_d < 2^24 and n <= 128: the general
@@ -38,11 +38,25 @@ struct LsArgs {
                        // by the launcher before every launch)
     int32_t key_l;     // > 0: n <= 2^key_l and n max_f max_d < 2^(30 - 2 key_l), so the
                        // tensor-core search packs a swap value and its pair in 32 bits
+    int32_t sym;       // F and D symmetric with zero diagonal
+    int32_t exact32;   // n max_f max_d < 2^27 and max_d <= 65535: the int32 SIMT search is exact
+    int32_t force;     // a LsKind chosen by the caller, or -1 (ls_kind decides)
 };
 
 // Which local-search kernel serves a population, and the launch shape.
-enum LsKind { LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_TEAM8N = 4, LS_GEN = 5, LS_KINDS = 6 };
+//   TEAM1/2/8: symmetric, tensor-core set-up, teams of 1, 2, 8 warps (n <= 32, 64, 128)
+//   TEAM8N:    the same with 8-bit staging (entries <= 255), 128 < n <= 160
+//   GEN:       any F, D (small entries), tensor-core set-up of R + C, n <= 128
+//   SIMT:      symmetric, int32 G from SIMT multiply-adds (n max_f max_d < 2^27)
+//   SIMT64:    symmetric, int64 G (any entries whose costs fit int64)
+//   DIRECT:    any F, D, int64, every swap value from the general O(n) formula
+enum LsKind {
+    LS_TEAM1 = 0, LS_TEAM2 = 1, LS_SIMT = 2, LS_TEAM8 = 3, LS_TEAM8N = 4, LS_GEN = 5,
+    LS_SIMT64 = 6, LS_DIRECT = 7, LS_KINDS = 8
+};
 LsKind ls_kind(const LsArgs& a);
+// whether `kind` is exact for the population described by `a` and serves its n
+bool ls_kind_serves(LsKind kind, const LsArgs& a);
 
 // One local-search launch over `count` populations of the same kind.
 struct LsLaunch {
@@ -55,8 +69,8 @@ struct LsLaunch {
     int total;             // particles over the table (automatic shape)
 };
 cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st);
-// largest n the local search serves (tc_flags: LsArgs::tc_exact of the instance)
-int ls_max_n(int tc_flags);
+// largest n a search kernel serves
+int ls_max_n(LsKind kind);
 
 // The velocity and position launches over `count` populations (flat index over
 // particles).
@@ -88,9 +102,13 @@ cudaError_t launch_bests(const StateView* d_views, int count, int m_max, int ini
 int bests_max_swarms();
 
 // Sorts `count` costs in `scratch` (>= next power of two entries) and writes
-// {min, p5, p25, p50, p75, max} to out6 and the mean to *mean (device pointers).
+// {min, p5, p25, p50, p75, max, sum low word, sum high word} to out8 (device
+// pointers; the sum of the costs as a 128-bit two's-complement integer).
 cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, int32_t scratch_len,
-                         int64_t* out6, double* mean, cudaStream_t st);
+                         int64_t* out8, cudaStream_t st);
+// Host: the mean of `count` values whose 128-bit sum is (sum_hi, sum_lo), as
+// floor-quotient plus remainder / count.
+double mean_of_sum(int64_t sum_lo, int64_t sum_hi, int32_t count);
 
 // Histogram of `count` device costs: counts (device, bins + 2, zeroed by the caller)
 // [0] below lo, [1 + b] for b = floor((cost - lo) bins / (hi - lo)), [bins + 1] >= hi.

@@ -22,6 +22,11 @@ int status_of(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// the result block of a state: the counters, then the best cost (8 bytes), its
+// iteration (4), padding (4) and the best permutation
+constexpr size_t kCntBytes = (CNT_N * 8 + 15) / 16 * 16;
+constexpr size_t kResHead = kCntBytes + 16;
+
 // host round-to-nearest-even float -> bfloat16 bits (finite inputs)
 uint16_t host_bf16(float f) {
     uint32_t b;
@@ -55,9 +60,8 @@ int validate(const qap_instance* inst, const pso_params_t* p) {
     if (p->mig_period < 1) return QAP_ERR_INVALID_ARG;
     if (p->v_storage != PSO_V_FP32 && p->v_storage != PSO_V_BF16) return QAP_ERR_INVALID_ARG;
     if (p->sx_kind != PSO_SXK_SECOND_TARGET && p->sx_kind != PSO_SXK_PICK_COLUMN) return QAP_ERR_INVALID_ARG;
-    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
-    if ((p->ls_max_moves >= 0) && !inst->sym_zd && !(inst->tc_exact & 4)) return QAP_ERR_UNSUPPORTED;
-    if (n > ls_max_n(inst->tc_exact) || n > velocity_sx_max_n(p->v_storage)) return QAP_ERR_UNSUPPORTED;
+    if (!inst->exact64) return QAP_ERR_OVERFLOW;  // costs or swap values could leave int64
+    if (n > velocity_sx_max_n(p->v_storage)) return QAP_ERR_UNSUPPORTED;
     return QAP_OK;
 }
 
@@ -79,6 +83,9 @@ LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work) {
     a.max_moves = (init && !s->prm.ls_at_init) ? -1 : s->prm.ls_max_moves;
     a.tc_exact = s->inst->tc_exact;
     a.key_l = s->inst->key_l;
+    a.sym = s->inst->sym_zd;
+    a.exact32 = s->inst->exact32 && s->inst->narrow_ok;
+    a.force = -1;
     a.work = work;
     return a;
 }
@@ -202,6 +209,9 @@ int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_insta
     q->max_d = md;
     q->exact32 = ((long double)n * mf * md < (long double)(1 << 27)) ? 1 : 0;
     q->narrow_ok = md <= 65535 ? 1 : 0;
+    // every cost (n^2 terms), every value of the search tables (n terms) and every swap
+    // value (8 n + 4 such terms) stays below 2^62 in magnitude: exact in int64
+    q->exact64 = ((long double)n * n + 8.0L * n + 4.0L) * mf * md < 4611686018427387904.0L ? 1 : 0;
     q->tc_exact = (sym && mf <= 2048 && md <= 2048 && (long double)n * mf * md < (long double)(1 << 24)) ? 1 : 0;
     if (q->tc_exact && mf <= 255 && md <= 255) q->tc_exact |= 2;
     if (!sym && n <= 128 && mf <= 2048 && md <= 2048 && 2.0L * n * mf * md < (long double)(1 << 24))
@@ -243,6 +253,7 @@ int qap_instance_info(qap_instance_t inst, qap_instance_info_t* out) {
     out->max_f = inst->max_f;
     out->max_d = inst->max_d;
     out->exact_int32 = inst->exact32;
+    out->exact_int64 = inst->exact64;
     return QAP_OK;
 }
 
@@ -316,11 +327,12 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     const size_t omoves = take((size_t)P * 4), orounds = take((size_t)P * 4);
     const size_t oPG = take((size_t)m * sv.ps), oPG2 = take((size_t)m * sv.ps);
     const size_t ocostG = take((size_t)m * 8), ocostG2 = take((size_t)m * 8);
-    // the best cost, its iteration and the best permutation side by side: pso_best reads
-    // them with one copy
-    const size_t ores = take(16 + (size_t)sv.ps), obc = ores, obi = ores + 8, obest = ores + 16;
+    // the counters, the best cost, its iteration and the best permutation side by side:
+    // pso_best reads them with one copy (and reports the kernels' error counter)
+    const size_t ores = take(kResHead + (size_t)sv.ps), ocnt = ores, obc = ores + kCntBytes,
+                 obi = obc + 8, obest = obc + 16;
     const size_t ot = take(4);
-    const size_t ocnt = take(CNT_N * 8), ostb = take((size_t)sl * 8), osto = take(7 * 8);
+    const size_t ostb = take((size_t)sl * 8), osto = take(8 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
     const size_t owork = take(3 * 4);  // search (iteration, set-up), position
     char* base = nullptr;
@@ -331,7 +343,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
         return status_of(e);
     }
     s->dbase = base;
-    e = cudaMallocHost(&s->h_res, 16 + (size_t)sv.ps);  // pinned: pso_best's read-back
+    e = cudaMallocHost(&s->h_res, kResHead + (size_t)sv.ps);  // pinned: pso_best's read-back
     if (e != cudaSuccess) {
         s->h_res = nullptr;
         pso_destroy(s);
@@ -410,7 +422,7 @@ int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
     const size_t a = 256;
     size_t t = align_up(P * vstride * esz, a) + 3 * align_up(P * ps, a) + 2 * align_up(P * 8, a) +
                2 * align_up(P * 4, a) + 2 * align_up(m * ps, a) + 2 * align_up(m * 8, a) + 4 * a +
-               align_up(CNT_N * 8, a) + align_up(sl * 8, a) + align_up(7 * 8, a) +
+               align_up(kResHead + ps, a) + align_up(sl * 8, a) + align_up(8 * 8, a) +
                align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a;
     *bytes = t;
     return QAP_OK;
@@ -459,15 +471,20 @@ int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t fl
 int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
     if (!s) return QAP_ERR_INVALID_ARG;
     const int n = s->sv.n;
-    // cost (8 bytes), iteration (4), padding (4), permutation (n): one copy
-    cudaError_t e = cudaMemcpyAsync(s->h_res, s->sv.best_cost, 16 + (size_t)n, cudaMemcpyDeviceToHost, s->stream);
+    // counters (kCntBytes), cost (8 bytes), iteration (4), padding (4), permutation (n):
+    // one copy
+    cudaError_t e = cudaMemcpyAsync(s->h_res, s->sv.counters, kResHead + (size_t)n, cudaMemcpyDeviceToHost,
+                                    s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return status_of(e);
+    unsigned long long errs = 0;
+    std::memcpy(&errs, s->h_res + 8 * CNT_ERR, 8);
+    if (errs) return QAP_ERR_TIMEOUT;  // a kernel gave up a bounded wait or skipped an access
     int64_t c = 0;
     int32_t it = 0;
-    std::memcpy(&c, s->h_res, 8);
-    std::memcpy(&it, s->h_res + 8, 4);
-    const uint8_t* p = s->h_res + 16;
+    std::memcpy(&c, s->h_res + kCntBytes, 8);
+    std::memcpy(&it, s->h_res + kCntBytes + 8, 4);
+    const uint8_t* p = s->h_res + kCntBytes + 16;
     if (cost) *cost = c;
     if (iter_found) *iter_found = it;
     if (perm)
@@ -476,13 +493,12 @@ int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
 }
 
 static int stats_of_range(pso_state_t s, int32_t first, int32_t count, pso_stats_t* out) {
-    cudaError_t e = launch_stats(s->sv.cost + first, count, s->stats_buf, s->stats_len, s->stats_out,
-                                 (double*)(s->stats_out + 6), s->stream);
-    int64_t o[7];
+    cudaError_t e = launch_stats(s->sv.cost + first, count, s->stats_buf, s->stats_len, s->stats_out, s->stream);
+    int64_t o[8];
     unsigned long long cnt[CNT_N];
     int64_t bc = 0;
     int32_t t = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(o, s->stats_out, 56, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(o, s->stats_out, sizeof(o), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, s->sv.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bc, s->sv.best_cost, 8, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&t, s->sv.t, 4, cudaMemcpyDeviceToHost, s->stream);
@@ -496,7 +512,7 @@ static int stats_of_range(pso_state_t s, int32_t first, int32_t count, pso_stats
     out->p50 = o[3];
     out->p75 = o[4];
     out->max = o[5];
-    std::memcpy(&out->mean, &o[6], 8);
+    out->mean = mean_of_sum(o[6], o[7], count);
     out->particle_iterations = (int64_t)cnt[CNT_PIT];
     out->ls_moves = (int64_t)cnt[CNT_MOVES];
     out->ls_rounds = (int64_t)cnt[CNT_ROUNDS];
@@ -671,7 +687,7 @@ int pso_import_state(pso_state_t s, const pso_host_state_t* in) {
     return status_of(e);
 }
 
-static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count, int32_t max_moves,
+static int run_ls_hook(qap_instance_t inst, int force, const int32_t* perms, int32_t count, int32_t max_moves,
                        int32_t* perms_out, int64_t* costs, int32_t* moves, int32_t* rounds) {
     const int n = inst->n;
     for (int c = 0; c < count; ++c) {
@@ -682,7 +698,21 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
             seen[v] = 1;
         }
     }
+    LsArgs a{};
+    a.n = n;
+    a.count = count;
+    a.F = inst->dF;
+    a.D = inst->dD;
+    a.max_moves = max_moves;
+    a.tc_exact = inst->tc_exact;
+    a.key_l = inst->key_l;
+    a.sym = inst->sym_zd;
+    a.exact32 = inst->exact32 && inst->narrow_ok;
+    a.force = force;
+    const LsKind kind = ls_kind(a);
+    if (!ls_kind_serves(kind, a)) return QAP_ERR_UNSUPPORTED;
     const int ps = (int)align_up(n, 16);
+    a.ps_in = a.ps_out = ps;
     std::vector<uint8_t> hp((size_t)count * ps, 0);
     for (int c = 0; c < count; ++c)
         for (int j = 0; j < n; ++j) hp[(size_t)c * ps + j] = (uint8_t)perms[(size_t)c * n + j];
@@ -697,25 +727,16 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
     if (e == cudaSuccess) e = cudaMalloc(&dr, (size_t)count * 4);
     if (e == cudaSuccess) e = cudaMemcpy(din, hp.data(), hp.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        LsArgs a{};
-        a.n = n;
-        a.count = count;
-        a.ps_in = a.ps_out = ps;
-        a.F = inst->dF;
-        a.D = inst->dD;
         a.in = din;
         a.out = dout;
         a.cost = dc;
         a.moves = dm;
         a.rounds = dr;
-        a.max_moves = max_moves;
-        a.tc_exact = inst->tc_exact;
-        a.key_l = inst->key_l;
         a.work = dw;
         LsArgs* da = nullptr;
         e = cudaMalloc(&da, sizeof(LsArgs));
         if (e == cudaSuccess) e = cudaMemcpy(da, &a, sizeof(LsArgs), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = launch_ls(LsLaunch{da, dw, 1, n, (int)ls_kind(a), 0, count}, 0);
+        if (e == cudaSuccess) e = launch_ls(LsLaunch{da, dw, 1, n, (int)kind, 0, count}, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(da);
     }
@@ -743,22 +764,56 @@ static int run_ls_hook(qap_instance_t inst, const int32_t* perms, int32_t count,
     return QAP_OK;
 }
 
+// the search kernel a QAP_SEARCH_* choice names for this instance (-1: automatic)
+static int forced_kind(const qap_instance* inst, int32_t kernel, int* out) {
+    LsArgs a{};
+    a.n = inst->n;
+    a.tc_exact = inst->tc_exact;
+    a.sym = inst->sym_zd;
+    a.exact32 = inst->exact32 && inst->narrow_ok;
+    a.force = -1;
+    switch (kernel) {
+        case QAP_SEARCH_AUTO: *out = -1; return QAP_OK;
+        case QAP_SEARCH_TENSOR: {
+            const LsKind k = !inst->sym_zd ? LS_GEN
+                             : inst->n <= 32 ? LS_TEAM1
+                             : inst->n <= 64 ? LS_TEAM2
+                             : inst->n <= 128 ? LS_TEAM8 : LS_TEAM8N;
+            *out = (int)k;
+            return ls_kind_serves(k, a) ? QAP_OK : QAP_ERR_UNSUPPORTED;
+        }
+        case QAP_SEARCH_SIMT: *out = (int)LS_SIMT; return ls_kind_serves(LS_SIMT, a) ? QAP_OK : QAP_ERR_UNSUPPORTED;
+        case QAP_SEARCH_INT64: {
+            const LsKind k = ls_kind_serves(LS_SIMT64, a) ? LS_SIMT64 : LS_DIRECT;
+            *out = (int)k;
+            return QAP_OK;
+        }
+        case QAP_SEARCH_DIRECT: *out = (int)LS_DIRECT; return QAP_OK;
+        default: return QAP_ERR_INVALID_ARG;
+    }
+}
+
 int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int64_t* out) {
-    if (!inst || !perms || !out || count < 0) return QAP_ERR_INVALID_ARG;
-    if (count == 0) return QAP_OK;
-    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
-    if (inst->n > ls_max_n(inst->tc_exact)) return QAP_ERR_UNSUPPORTED;
-    return run_ls_hook(inst, perms, count, -1, nullptr, out, nullptr, nullptr);
+    return qap_search_with(inst, QAP_SEARCH_AUTO, const_cast<int32_t*>(perms), count, -1, out, nullptr, nullptr);
 }
 
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds) {
-    if (!inst || !perms || count < 0 || max_moves < 0) return QAP_ERR_INVALID_ARG;
+    if (max_moves < 0) return QAP_ERR_INVALID_ARG;
+    return qap_search_with(inst, QAP_SEARCH_AUTO, perms, count, max_moves, costs, moves, rounds);
+}
+
+int qap_search_with(qap_instance_t inst, int32_t kernel, int32_t* perms, int32_t count, int32_t max_moves,
+                    int64_t* costs, int32_t* moves, int32_t* rounds) {
+    if (!inst || !perms || count < 0) return QAP_ERR_INVALID_ARG;
+    if (max_moves < 0 && !costs) return QAP_ERR_INVALID_ARG;
+    if (!inst->exact64) return QAP_ERR_OVERFLOW;
+    int force = -1;
+    const int st = forced_kind(inst, kernel, &force);
+    if (st != QAP_OK) return st;
     if (count == 0) return QAP_OK;
-    if (!inst->narrow_ok || !inst->exact32) return QAP_ERR_OVERFLOW;
-    if (!inst->sym_zd && !(inst->tc_exact & 4)) return QAP_ERR_UNSUPPORTED;
-    if (inst->n > ls_max_n(inst->tc_exact)) return QAP_ERR_UNSUPPORTED;
-    return run_ls_hook(inst, perms, count, max_moves, perms, costs, moves, rounds);
+    return run_ls_hook(inst, force, perms, count, max_moves, max_moves < 0 ? nullptr : perms, costs, moves,
+                       rounds);
 }
 
 int qap_delta_table(qap_instance_t inst, const int32_t* perm, int64_t* out) {

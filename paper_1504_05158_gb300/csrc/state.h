@@ -13,7 +13,8 @@ struct qap_instance {
     int32_t* dD;
     int32_t sym_zd;
     int32_t max_f, max_d;
-    int32_t exact32;
+    int32_t exact32;    // n max_f max_d < 2^27
+    int32_t exact64;    // (n^2 + 8 n + 4) max_f max_d < 2^62: every cost and swap value fits int64
     int32_t narrow_ok;  // every entry fits the uint16 staging of the kernels
     int32_t tc_exact;   // bit 0: the tensor-core set-up of the local search is exact; bit 1: and 8-bit staging fits
     int32_t key_l;      // pair-index bits of the 32-bit search keys, 0 when |delta| is not bounded enough

@@ -9,7 +9,7 @@
 namespace {
 
 constexpr int kSortLen = QAP_NOALLOC_MAX_COUNT;  // power of two
-constexpr int kResult = 8;                        // 6 percentiles, the mean, padding
+constexpr int kResult = 8;                        // 6 percentiles, the 128-bit sum
 
 // The only device memory this entry point uses. In host code this name is a
 // host-side stand-in: its device address comes from cudaGetSymbolAddress.
@@ -51,12 +51,12 @@ extern "C" int qap_cost_stats_noalloc(const int64_t* costs, int32_t count, void*
     int64_t* res = scratch + kSortLen;
     // the kernel rewrites scratch[0, len) and the result slots on every call, so
     // nothing left by an earlier call is read
-    e = qap::launch_stats(costs, count, scratch, len, res, reinterpret_cast<double*>(res + 6), st);
-    int64_t host[7];
+    e = qap::launch_stats(costs, count, scratch, len, res, st);
+    int64_t host[kResult];
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return QAP_ERR_CUDA;
     for (int i = 0; i < 6; ++i) out6[i] = host[i];
-    __builtin_memcpy(mean, &host[6], sizeof(double));
+    *mean = qap::mean_of_sum(host[6], host[7], count);
     return QAP_OK;
 }

@@ -21,6 +21,7 @@ TIE_RANDOM, TIE_FIRST = 0, 1
 MIG_NONE, MIG_RANK, MIG_RING = 0, 1, 2
 V_FP32, V_BF16 = 0, 1
 SXK_SECOND_TARGET, SXK_PICK_COLUMN = 0, 1
+SEARCH_AUTO, SEARCH_TENSOR, SEARCH_SIMT, SEARCH_INT64, SEARCH_DIRECT = range(5)
 
 # every exported symbol of include/qap_pso.h
 EXPORTS = [
@@ -29,7 +30,8 @@ EXPORTS = [
     "pso_export_state", "pso_import_state", "qap_eval_costs", "qap_local_search",
     "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
     "pso_batch_size", "pso_batch_member", "pso_batch_destroy", "pso_footprint", "pso_poll",
-    "qap_delta_table", "pso_discretize", "pso_stats_swarm", "pso_cost_histogram",
+    "qap_delta_table", "pso_discretize", "pso_stats_swarm", "pso_cost_histogram", "qap_search_with",
+    "qap_int32_peak",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -71,7 +73,7 @@ class Stats(C.Structure):
 
 class InstanceInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("symmetric_zero_diag", C.c_int32), ("max_f", C.c_int32),
-                ("max_d", C.c_int32), ("exact_int32", C.c_int32)]
+                ("max_d", C.c_int32), ("exact_int32", C.c_int32), ("exact_int64", C.c_int32)]
 
 
 class HostState(C.Structure):
@@ -114,6 +116,8 @@ def lib():
         L.pso_import_state.argtypes = [vp, C.POINTER(HostState)]
         L.qap_eval_costs.argtypes = [vp, vp, C.c_int32, vp]
         L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.qap_search_with.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.qap_int32_peak.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.qap_cost_stats_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double)]
         L.pso_batch_create.argtypes = [C.c_int32, vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
         L.pso_batch_step.argtypes = [vp, C.c_int32]
@@ -172,6 +176,15 @@ def cost_stats_noalloc(costs_dev_ptr, count, stream=None):
                 p75=int(out[4]), max=int(out[5]), mean=mean.value)
 
 
+def int32_peak(stream=None):
+    """Measured integer throughput of the current GPU: (multiply-add lane operations/s
+    counting two per multiply-add, add lane operations/s)."""
+    mad, add = C.c_double(), C.c_double()
+    st = C.c_void_p(stream) if stream else None
+    _check(lib().qap_int32_peak(st, C.byref(mad), C.byref(add)), "qap_int32_peak")
+    return mad.value, add.value
+
+
 def footprint(n, params):
     """Device bytes a population of size n with these parameters allocates."""
     b = C.c_size_t()
@@ -211,6 +224,18 @@ class Instance:
         rounds = np.zeros(k, np.int32)
         _check(lib().qap_local_search(self.h, _ptr(perms), k, max_moves, _ptr(costs), _ptr(moves),
                                       _ptr(rounds)), "qap_local_search")
+        return perms, costs, moves, rounds
+
+    def search_with(self, kernel, perms, max_moves=0):
+        """The goal function (max_moves < 0) or the local search on the named search
+        kernel (SEARCH_*); returns (perms, costs, moves, rounds)."""
+        perms = np.ascontiguousarray(perms, np.int32).reshape(-1, self.n).copy()
+        k = len(perms)
+        costs = np.zeros(k, np.int64)
+        moves = np.zeros(k, np.int32)
+        rounds = np.zeros(k, np.int32)
+        _check(lib().qap_search_with(self.h, kernel, _ptr(perms), k, max_moves, _ptr(costs), _ptr(moves),
+                                     _ptr(rounds)), "qap_search_with")
         return perms, costs, moves, rounds
 
     def delta_table(self, perm):

@@ -43,6 +43,7 @@ class Result:
     arrival_s: float
     admit_s: float
     done_s: float
+    error: str | None = None  # set when the device reported a failure: no result
 
     @property
     def latency_s(self):
@@ -79,10 +80,13 @@ class ServeReport:
         return lat[k]
 
     def particle_iterations(self):
-        return sum(r.particles * r.iterations for r in self.results)
+        return sum(r.particles * r.iterations for r in self.results if r.error is None)
+
+    def failed(self):
+        return [r for r in self.results if r.error is not None]
 
     def summary(self):
-        return {"requests": len(self.results), "makespan_s": self.makespan_s,
+        return {"requests": len(self.results), "failed": len(self.failed()), "makespan_s": self.makespan_s,
                 "p50_s": self.percentile(0.5), "p99_s": self.percentile(0.99),
                 "particle_iterations_per_s": self.particle_iterations() / max(self.makespan_s, 1e-9),
                 "peak_bytes": self.peak_bytes, "peak_slots": self.peak_slots,
@@ -155,10 +159,16 @@ class Server:
             still = []
             for s in active:
                 if s.queued >= s.job.iterations and s.idle:
-                    cost, perm, it = s.swarm.best()
+                    # a kernel that gave up a bounded wait makes best() fail: the
+                    # request fails instead of returning a possibly incomplete result
+                    try:
+                        cost, perm, it = s.swarm.best()
+                        err = None
+                    except Q.QapError as e:
+                        cost, perm, it, err = None, None, -1, str(e)
                     rep.results.append(Result(s.job.rid, s.swarm.n, s.swarm.P, s.job.iterations, cost,
                                               perm, it, s.job.arrival_s if realtime else 0.0,
-                                              s.admit_s, self.clock() - t0))
+                                              s.admit_s, self.clock() - t0, err))
                     s.swarm.close()
                     s.inst.close()
                     used -= s.bytes

@@ -194,7 +194,7 @@ def test_swarm_stats_and_histogram(Q):
             want = O.stats(cost[k * 37:(k + 1) * 37])
             keys = ("min", "p5", "p25", "p50", "p75", "max")
             assert [got[x] for x in keys] == [want[x] for x in keys]
-            assert abs(got["mean"] - want["mean"]) <= 1e-9 * abs(want["mean"])
+            assert got["mean"] == want["mean"]
         lo, hi = int(cost.min()) + 17, int(cost.max()) - 5
         for bins, swarm in ((1, -1), (7, -1), (50, 3)):
             sel = cost if swarm < 0 else cost[swarm * 37:(swarm + 1) * 37]

@@ -376,6 +376,20 @@ def test_stats_nearest_rank():
         assert abs(st["mean"] - c.mean()) <= 1e-9 * abs(c.mean())
 
 
+def test_stats_mean_exact_for_huge_costs():
+    # costs near the int64 limit: their sum leaves int64, yet the mean is the exact
+    # rational sum / P to within one rounding of a double
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    for P in (1, 3, 64, 1001):
+        c = rng.integers(2**62, 2**63 - 1, P, dtype=np.int64)
+        exact = Fraction(sum(int(x) for x in c), P)
+        got = O.stats(c)["mean"]
+        assert abs(Fraction(got) - exact) <= exact * Fraction(1, 2**52)
+    c = np.array([-7, 2, 0], np.int64)  # a negative total: remainder of the truncated quotient
+    assert abs(Fraction(O.stats(c)["mean"]) - Fraction(-5, 3)) <= Fraction(5, 3) * Fraction(1, 2**52)
+
+
 # ------------------------------------------------------------------ whole runs
 
 def test_tiny9_reaches_brute_force_optimum():
@@ -499,3 +513,17 @@ def test_histogram_by_brute_force():
                     b += 1
                 want[1 + b] += 1
         assert np.array_equal(got, want) and got.sum() == P
+
+
+def test_parallel_step_equals_step():
+    # the all-cores form of the oracle's iteration (the CPU baseline) is the same
+    # computation: identical state after a few iterations, with migration
+    inst = W.dense_uniform(12, 4)
+    q = O.make_params(swarms=4, swarm_size=9, mig_kind=1, mig_depth=1)
+    a = O.init(q, inst.F, inst.D, 31)
+    b = a.copy()
+    O.step(q, inst.F, inst.D, 31, a, 4)
+    O.step_parallel(q, inst.F, inst.D, 31, b, 4, threads=4)
+    for k in ("V", "X", "PL", "costL", "cost", "PG", "costG", "best_p", "best_cost", "best_iter", "t",
+              "counters", "moves"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k

@@ -132,3 +132,23 @@ def test_report_percentiles():
     s = rep.summary()
     assert s["p50_s"] == 50.0 and s["p99_s"] == 99.0
     assert s["particle_iterations_per_s"] == 100 * 10 * 30 / 10.0
+
+
+def test_device_failure_fails_the_request(fake, monkeypatch):
+    # a population whose kernels reported an error (pso_best returns a status) fails
+    # its request; the others complete and the memory is returned
+    def best(self):
+        if self.seed == 3:
+            raise S.Q.QapError(S.Q.ERR_TIMEOUT, "pso_best")
+        return int(self.seed) * 10, np.arange(self.n), 1
+    monkeypatch.setattr(FakeSwarm, "best", best)
+    monkeypatch.setattr(S.Q, "status_string", lambda st: "device wait timed out")
+    F = np.zeros((8, 8), np.int32)
+    jobs = [S.Job(i, 0.0, F, F, P(2, 4), seed=i, iterations=3) for i in range(6)]
+    rep = S.Server(budget_bytes=10**9, clock=FakeClock()).run(jobs, realtime=False)
+    assert len(rep.results) == 6
+    bad = rep.failed()
+    assert [r.rid for r in bad] == [3] and bad[0].best_cost is None and "timed out" in bad[0].error
+    assert all(r.best_cost == r.rid * 10 for r in rep.results if r.rid != 3)
+    assert rep.summary()["failed"] == 1
+    assert FakeSwarm.live == 0

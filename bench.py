@@ -493,14 +493,15 @@ def run_batch(args, quick=False):
     insts = W.uneven_batch(64)
     gis = [Q.Instance(i.F, i.D) for i in insts]
     prm = [Q.default_params(swarms=8, swarm_size=256, v_storage=Q.V_BF16) for _ in insts]
-    b = Q.Batch(gis, prm, [4096 + i for i in range(len(insts))], autotune=True)
+    bstream = torch.cuda.Stream()
+    b = Q.Batch(gis, prm, [4096 + i for i in range(len(insts))], stream=bstream.cuda_stream, autotune=True)
     warm, steps = (5, 20) if quick else (args.warmup, args.steps)
     b.step(warm)
     torch.cuda.synchronize()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
     # the whole-batch rate from graph replays (the path pso_batch_step takes), then a
     # per-phase breakdown launched kernel by kernel
-    stream = torch.cuda.current_stream()
+    stream = bstream  # the batch's own stream: its launches and the events
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         a.record(stream)

@@ -197,7 +197,64 @@ int pso_stats_swarm(pso_state_t st, int32_t swarm, pso_stats_t* out);
  * 1 <= bins <= 2^20, lo < hi. Synchronous. Errors: QAP_ERR_INVALID_ARG. */
 int pso_cost_histogram(pso_state_t st, int32_t swarm, int64_t lo, int64_t hi, int32_t bins, int64_t* counts);
 
+/* Per-iteration statistics recorded on the device (section 4.2: the percentile
+ * ranks of Figs. 4 and 5, the probability mass function of Figs. 6 and 7). After
+ * pso_trace_start, every iteration of pso_step appends one record to a ring of
+ * `capacity` records in device memory (the captured iterations are re-captured with
+ * one more kernel); the host reads them with one copy. A record is `len` =
+ * 9 + 8 m + bins + 2 int64 words:
+ *   [0]              completed iterations t after the iteration recorded;
+ *   [1 .. 8]         the population's current costs: min, p5, p25, p50, p75, max
+ *                    (nearest rank, as pso_stats) and their exact sum as a 128-bit
+ *                    two's-complement integer (low word, then high word);
+ *   [9 + 8k .. +8]   the same eight words for swarm k, 0 <= k < m;
+ *   [9 + 8m ..]      the histogram of pso_cost_histogram over every particle: below
+ *                    lo, bins equal-width bins of [lo, hi), at or above hi.
+ * Allocates the ring (capacity * len * 8 bytes); synchronises the state's stream.
+ * Batch members and swarms larger than 16384 particles are not traced
+ * (QAP_ERR_UNSUPPORTED). pso_step_timed does not record. Errors:
+ * QAP_ERR_INVALID_ARG (capacity < 1, bins outside [1, 2^20], hi <= lo), QAP_ERR_OOM. */
+int pso_trace_start(pso_state_t st, int32_t capacity, int64_t lo, int64_t hi, int32_t bins);
+/* Words per record of the running trace. */
+int pso_trace_record_len(pso_state_t st, int32_t* len);
+/* Copies the most recent min(recorded, capacity, max_records) records, oldest first,
+ * into `records` (host, max_records * len int64); *count receives how many.
+ * Synchronises. */
+int pso_trace_read(pso_state_t st, int64_t* records, int32_t max_records, int32_t* count);
+/* Stops recording and frees the ring (synchronises). */
+int pso_trace_stop(pso_state_t st);
+
 void pso_destroy(pso_state_t st);
+
+/* ------------------------------------------------ parts of a run (one per process) */
+/* A run of M swarms may be split by whole swarms over several processes (one GPU
+ * each): swarms are independent within an iteration (section 3.2) and meet only in
+ * the migration step, which moves one permutation per swarm. pso_init_part
+ * allocates the part holding swarms [first_swarm, first_swarm + params->swarms) of
+ * the run: every random draw uses the swarm's index in the whole run, so each
+ * particle evolves exactly as in the unsplit run. The part does no migration
+ * (params->mig_kind is ignored); the caller migrates between the parts with the
+ * calls below (the exchange: the swarm-best costs of every part, then one
+ * permutation per migrating swarm). Errors as pso_init. */
+int pso_init_part(qap_instance_t inst, const pso_params_t* params, uint64_t seed, int32_t first_swarm,
+                  void* stream, pso_state_t* out);
+/* The swarm bests P^G of the state's m swarms: costs (host, m int64) and, if perms is
+ * not NULL, the permutations (host, m x n int32). Synchronises. */
+int pso_swarm_bests(pso_state_t st, int64_t* costs, int32_t* perms);
+/* Replaces swarm `swarm`'s best P^G by (cost, perm) (a migrated solution, accepted
+ * even if worse, section 3.2). perm: host, n int32. Synchronises (after the queued
+ * work). Errors: QAP_ERR_INVALID_ARG (swarm out of range, perm not a permutation). */
+int pso_set_swarm_best(pso_state_t st, int32_t swarm, int64_t cost, const int32_t* perm);
+/* The current position and cost of particle `index` (swarm-major: swarm * swarm_size
+ * + particle in swarm, within the state). Synchronises. */
+int pso_particle(pso_state_t st, int32_t index, int64_t* cost, int32_t* perm);
+/* The counter-based generator every draw of an iteration uses (Philox4x32-10,
+ * Salmon et al., SC'11): key = (seed low 32 bits, seed high 32 bits), counter = (c0,
+ * c1, c2, tag << 24 | block), tag < 256, block < 2^24. out4: host, 4 uint32. Host
+ * code; for callers that reproduce a draw (the migration picks of a split run:
+ * tag 4, counter (k, 0, t)). */
+int qap_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t tag, uint32_t block,
+               uint32_t* out4);
 
 /* ------------------------------------------------ state export / import */
 /* Host copies of the whole state, e.g. for checkpoints and for comparing one

@@ -170,6 +170,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
             pso_batch_destroy(b);
             return st;
         }
+        s->borrowed = true;
         b->members.push_back(s);
     }
     // tables over all members

@@ -19,12 +19,20 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
-__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                      uint32_t k0, uint32_t k1) {
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = mulhi32(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = mulhi32(0xCD9E8D57u, c2);
         const uint32_t n0 = hi1 ^ c1 ^ k0;
         const uint32_t n2 = hi0 ^ c3 ^ k1;
         c0 = n0;
@@ -39,8 +47,8 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
 
 enum : uint32_t { TAG_R = 0, TAG_TIE = 1, TAG_INIT_X = 2, TAG_INIT_V = 3, TAG_MIG = 4, TAG_COLUMNS = 7 };
 
-__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
-                                    uint32_t tag, uint32_t block) {
+__host__ __device__ __forceinline__ U4 draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                                             uint32_t tag, uint32_t block) {
     return philox(c0, c1, c2, (tag << 24) | (block & 0xFFFFFFu), (uint32_t)seed,
                   (uint32_t)(seed >> 32));
 }
@@ -52,7 +60,7 @@ __device__ __forceinline__ uint32_t word_of(const U4& u, int i) {
 // top 24 bits as a fraction in [0, 1); exact in fp32
 __device__ __forceinline__ float u01f(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
 // floor(u * k / 2^32) in [0, k)
-__device__ __forceinline__ uint32_t below(uint32_t u, uint32_t k) {
+__host__ __device__ __forceinline__ uint32_t below(uint32_t u, uint32_t k) {
     return (uint32_t)(((uint64_t)u * (uint64_t)k) >> 32);
 }
 
@@ -178,6 +186,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // never change after pso_init, so captured graphs stay valid.
 struct StateView {
     int32_t n, m, ss, P;
+    int32_t swarm_base;  // index of swarm 0 of this population in the whole run (a part of a
+                         // run split over processes); the Philox counters use base + local
     int32_t ps;       // bytes between consecutive permutations (>= n, multiple of 16)
     int64_t vstride;  // elements between consecutive particles' V tiles (multiple of 8)
     void* V;          // P tiles of n x n, row = location, column = facility

@@ -59,7 +59,8 @@ __global__ void k_init(StateView s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = s.n;
     for (int p = blockIdx.x * kWarps + warp; p < s.P; p += gridDim.x * kWarps) {
-        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        // draws are keyed by the swarm's index in the whole run (swarm_base + local)
+        const uint32_t swarm = (uint32_t)(s.swarm_base + p / s.ss), pis = (uint32_t)(p % s.ss);
         if (lane == 0) {
             uint8_t* q = perm[warp];
             for (int i = 0; i < n; ++i) q[i] = (uint8_t)i;
@@ -774,14 +775,15 @@ __global__ void __launch_bounds__(kVelWarps * 32)
         const int fn = next_active(f + gridDim.x);
         const int n = s.n;
         const uint32_t t = (uint32_t)*s.t;
-        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        const int lsw = p / s.ss;  // the swarm in this population; draws use its index in the run
+        const uint32_t swarm = (uint32_t)(s.swarm_base + lsw), pis = (uint32_t)(p % s.ss);
         int pic[NW], plc[NW], pgc[NW];
 #pragma unroll
         for (int c = 0; c < NW; ++c) {
             const int j = lane + 32 * c;
             pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
             plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+            pgc[c] = j < n ? s.PG[(size_t)lsw * s.ps + j] : -1;
         }
         if (tid == 0) {  // one draw per particle, shared through shared memory
             const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
@@ -935,14 +937,15 @@ __global__ void __launch_bounds__(128)
         const int n = s.n;
         VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
         const uint32_t t = (uint32_t)*s.t;
-        const uint32_t swarm = (uint32_t)(p / s.ss), pis = (uint32_t)(p % s.ss);
+        const int lsw = p / s.ss;  // the swarm in this population; draws use its index in the run
+        const uint32_t swarm = (uint32_t)(s.swarm_base + lsw), pis = (uint32_t)(p % s.ss);
         int pic[NW], plc[NW], pgc[NW];
 #pragma unroll
         for (int c = 0; c < NW; ++c) {
             const int j = lane + 32 * c;
             pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
             plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[c] = j < n ? s.PG[(size_t)swarm * s.ps + j] : -1;
+            pgc[c] = j < n ? s.PG[(size_t)lsw * s.ps + j] : -1;
         }
         const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
         const Split a = exact_mul(s.c2, u01f(ur.x)), b = exact_mul(s.c3, u01f(ur.y));
@@ -1038,7 +1041,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         const uint32_t t = (uint32_t)*s.t;
         const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
         const bool sx_only = s.sx_only != 0;
-        const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(p / s.ss);
+        const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(s.swarm_base + p / s.ss);
         const uint32_t pis = sx_only ? (uint32_t)s.sx_pis[p] : (uint32_t)(p % s.ss);
         const VT* Vg = reinterpret_cast<const VT*>(s.V) + (size_t)p * s.vstride;
         // the tile -> shared memory with one bulk copy (tile padded to 16 bytes)

@@ -110,6 +110,18 @@ cudaError_t launch_stats(const int64_t* cost, int32_t count, int64_t* scratch, i
 // floor-quotient plus remainder / count.
 double mean_of_sum(int64_t sum_lo, int64_t sum_hi, int32_t count);
 
+// Per-iteration statistics of a population, recorded on the device into a ring of
+// `capacity` records of `len` int64 words (layout in trace.cu).
+struct TraceBuf {
+    int64_t* d = nullptr;  // [0] records written, then capacity records
+    int32_t capacity = 0, len = 0, bins = 0;
+    int64_t lo = 0, hi = 0;
+};
+// After the iteration's bookkeeping (the iteration counter already advanced).
+cudaError_t launch_trace(const StateView& s, const TraceBuf& tb, cudaStream_t st);
+// largest swarm size the trace kernel sorts in shared memory
+int trace_max_swarm();
+
 // Histogram of `count` device costs: counts (device, bins + 2, zeroed by the caller)
 // [0] below lo, [1 + b] for b = floor((cost - lo) bins / (hi - lo)), [bins + 1] >= hi.
 cudaError_t launch_histogram(const int64_t* cost, int count, int64_t lo, int64_t hi, int bins,

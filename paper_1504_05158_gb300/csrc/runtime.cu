@@ -153,7 +153,9 @@ cudaError_t enqueue_iteration(pso_state* s) {
     if (e != cudaSuccess) return e;
     e = launch_ls(s->ls_iter, s->stream);
     if (e != cudaSuccess) return e;
-    return launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
+    e = launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
+    if (e == cudaSuccess && s->trace.d) e = launch_trace(s->sv, s->trace, s->stream);
+    return e;
 }
 
 cudaError_t capture(pso_state* s, int iters, cudaGraphExec_t* out) {
@@ -172,6 +174,9 @@ cudaError_t capture(pso_state* s, int iters, cudaGraphExec_t* out) {
 }
 
 }  // namespace
+
+static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t seed, int32_t first_swarm,
+                      bool part, void* stream, pso_state_t* out);
 
 extern "C" {
 
@@ -282,13 +287,27 @@ void pso_params_default(pso_params_t* p) {
 
 int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, void* stream,
              pso_state_t* out) {
-    if (!inst || !params || !out) return QAP_ERR_INVALID_ARG;
+    return init_state(inst, params, seed, 0, false, stream, out);
+}
+
+int pso_init_part(qap_instance_t inst, const pso_params_t* params, uint64_t seed, int32_t first_swarm,
+                  void* stream, pso_state_t* out) {
+    return init_state(inst, params, seed, first_swarm, true, stream, out);
+}
+
+}  // extern "C"
+
+static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t seed, int32_t first_swarm,
+                      bool part, void* stream, pso_state_t* out) {
+    if (!inst || !params || !out || first_swarm < 0) return QAP_ERR_INVALID_ARG;
     int v = validate(inst, params);
     if (v != QAP_OK) return v;
     pso_state* s = new (std::nothrow) pso_state();
     if (!s) return QAP_ERR_OOM;
     s->inst = inst;
     s->prm = *params;
+    if (part) s->prm.mig_kind = PSO_MIG_NONE;  // a part of a run: the caller migrates
+    params = &s->prm;
     s->seed = seed;
     if (stream) {
         s->stream = (cudaStream_t)stream;
@@ -308,6 +327,7 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     sv.m = m;
     sv.ss = ss;
     sv.P = P;
+    sv.swarm_base = first_swarm;
     sv.ps = (int32_t)align_up(n, 16);
     sv.vstride = (int64_t)align_up((size_t)n * n, 8);
     const size_t esz = params->v_storage == PSO_V_BF16 ? 2 : 4;
@@ -411,6 +431,8 @@ int pso_init(qap_instance_t inst, const pso_params_t* params, uint64_t seed, voi
     *out = s;
     return QAP_OK;
 }
+
+extern "C" {
 
 int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
     if (!p || !bytes || n < 2 || n > 256 || p->swarms < 1 || p->swarm_size < 1) return QAP_ERR_INVALID_ARG;
@@ -553,6 +575,7 @@ void pso_destroy(pso_state_t s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->g1) cudaGraphExecDestroy(s->g1);
     if (s->g16) cudaGraphExecDestroy(s->g16);
+    if (s->trace.d) cudaFree(s->trace.d);
     cudaFree(s->dbase);
     if (s->h_res) cudaFreeHost(s->h_res);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -683,6 +706,9 @@ int pso_import_state(pso_state_t s, const pso_host_state_t* in) {
     cp(sv.best_cost, &in->best_cost, 8);
     cp(sv.best_iter, &in->best_iter, 4);
     cp(sv.t, &in->t, 4);
+    // recorded statistics belong to the replaced run
+    if (e == cudaSuccess && s->trace.d)
+        e = cudaMemsetAsync(s->trace.d, 0, 8 * (size_t)s->trace.capacity * s->trace.len, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return status_of(e);
 }
@@ -929,6 +955,70 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     if (cnt[CNT_ERR]) return QAP_ERR_TIMEOUT;
     for (int i = 0; i < count; ++i)
         for (int j = 0; j < n; ++j) out_perm[(size_t)i * n + j] = hz[(size_t)i * ps + j];
+    return QAP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ parts of a run (multi-process)
+extern "C" {
+
+int pso_swarm_bests(pso_state_t s, int64_t* costs, int32_t* perms) {
+    if (!s || !costs) return QAP_ERR_INVALID_ARG;
+    const StateView& sv = s->sv;
+    std::vector<uint8_t> pg((size_t)sv.m * sv.ps);
+    cudaError_t e = cudaMemcpyAsync(costs, sv.costG, (size_t)sv.m * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && perms)
+        e = cudaMemcpyAsync(pg.data(), sv.PG, pg.size(), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return status_of(e);
+    if (perms)
+        for (int k = 0; k < sv.m; ++k)
+            for (int j = 0; j < sv.n; ++j) perms[(size_t)k * sv.n + j] = pg[(size_t)k * sv.ps + j];
+    return QAP_OK;
+}
+
+int pso_set_swarm_best(pso_state_t s, int32_t swarm, int64_t cost, const int32_t* perm) {
+    if (!s || !perm || swarm < 0 || swarm >= s->sv.m) return QAP_ERR_INVALID_ARG;
+    const StateView& sv = s->sv;
+    std::vector<uint8_t> row(sv.ps, 0);
+    std::vector<char> seen(sv.n, 0);
+    for (int j = 0; j < sv.n; ++j) {
+        if (perm[j] < 0 || perm[j] >= sv.n || seen[perm[j]]) return QAP_ERR_INVALID_ARG;
+        seen[perm[j]] = 1;
+        row[j] = (uint8_t)perm[j];
+    }
+    // after the queued work, then synchronously (the host buffers are locals)
+    cudaError_t e = cudaMemcpyAsync(sv.PG + (size_t)swarm * sv.ps, row.data(), sv.n, cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv.costG + swarm, &cost, 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return status_of(e);
+}
+
+int pso_particle(pso_state_t s, int32_t index, int64_t* cost, int32_t* perm) {
+    if (!s || !cost || !perm || index < 0 || index >= s->sv.P) return QAP_ERR_INVALID_ARG;
+    const StateView& sv = s->sv;
+    std::vector<uint8_t> row(sv.ps);
+    int64_t c = 0;
+    cudaError_t e = cudaMemcpyAsync(row.data(), sv.X + (size_t)index * sv.ps, sv.ps, cudaMemcpyDeviceToHost,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, sv.cost + index, 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return status_of(e);
+    *cost = c;
+    for (int j = 0; j < sv.n; ++j) perm[j] = row[j];
+    return QAP_OK;
+}
+
+int qap_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t tag, uint32_t block,
+               uint32_t* out4) {
+    if (!out4 || tag > 255 || block > 0xFFFFFFu) return QAP_ERR_INVALID_ARG;
+    const U4 u = draw(seed, c0, c1, c2, tag, block);
+    out4[0] = u.x;
+    out4[1] = u.y;
+    out4[2] = u.z;
+    out4[3] = u.w;
     return QAP_OK;
 }
 

@@ -42,6 +42,8 @@ struct pso_state {
     qap::VsxLaunch vsx;
     qap::LsLaunch ls_iter, ls_init;
     cudaGraphExec_t g1, g16;
+    bool borrowed;            // a member of a batch (the batch runs its iterations)
+    qap::TraceBuf trace;      // per-iteration statistics (off unless pso_trace_start)
     unsigned char* h_res;     // pinned: best cost, iteration and permutation (pso_best)
 };
 

@@ -31,7 +31,8 @@ EXPORTS = [
     "qap_cost_stats_noalloc", "pso_batch_create", "pso_batch_step", "pso_batch_step_timed",
     "pso_batch_size", "pso_batch_member", "pso_batch_destroy", "pso_footprint", "pso_poll",
     "qap_delta_table", "pso_discretize", "pso_stats_swarm", "pso_cost_histogram", "qap_search_with",
-    "qap_int32_peak",
+    "qap_int32_peak", "pso_trace_start", "pso_trace_record_len", "pso_trace_read", "pso_trace_stop",
+    "pso_init_part", "pso_swarm_bests", "pso_set_swarm_best", "pso_particle", "qap_philox",
 ]
 NOALLOC_MAX_COUNT = 65536
 
@@ -118,6 +119,15 @@ def lib():
         L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.qap_search_with.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.qap_int32_peak.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.pso_trace_start.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.c_int32]
+        L.pso_trace_record_len.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.pso_trace_read.argtypes = [vp, vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.pso_trace_stop.argtypes = [vp]
+        L.pso_init_part.argtypes = [vp, C.POINTER(Params), C.c_uint64, C.c_int32, vp, C.POINTER(vp)]
+        L.pso_swarm_bests.argtypes = [vp, vp, vp]
+        L.pso_set_swarm_best.argtypes = [vp, C.c_int32, C.c_int64, vp]
+        L.pso_particle.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), vp]
+        L.qap_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, vp]
         L.qap_cost_stats_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double)]
         L.pso_batch_create.argtypes = [C.c_int32, vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
         L.pso_batch_step.argtypes = [vp, C.c_int32]
@@ -183,6 +193,13 @@ def int32_peak(stream=None):
     st = C.c_void_p(stream) if stream else None
     _check(lib().qap_int32_peak(st, C.byref(mad), C.byref(add)), "qap_int32_peak")
     return mad.value, add.value
+
+
+def philox(seed, c0, c1, c2, tag, block):
+    """The library's Philox4x32-10 draw (host code): four uint32 words."""
+    out = np.zeros(4, np.uint32)
+    _check(lib().qap_philox(seed, c0, c1, c2, tag, block, _ptr(out)), "qap_philox")
+    return out
 
 
 def footprint(n, params):
@@ -276,7 +293,10 @@ def discretize(Y, Z, params: Params, seed: int, swarm, particle, t: int):
 class Swarm:
     """Population state of one PSO run on the device."""
 
-    def __init__(self, inst: Instance, params: Params, seed: int, stream=None, _handle=None):
+    def __init__(self, inst: Instance, params: Params, seed: int, stream=None, _handle=None,
+                 first_swarm=None):
+        """first_swarm: the state is the part of a larger run holding swarms
+        first_swarm .. first_swarm + params.swarms - 1 (pso_init_part; no migration)."""
         self.inst = inst  # keeps the instance alive
         self.params = params
         self.n = inst.n
@@ -287,8 +307,31 @@ class Swarm:
             return
         h = C.c_void_p()
         st = C.c_void_p(stream) if stream else None
-        _check(lib().pso_init(inst.h, C.byref(params), seed, st, C.byref(h)), "pso_init")
+        if first_swarm is None:
+            _check(lib().pso_init(inst.h, C.byref(params), seed, st, C.byref(h)), "pso_init")
+        else:
+            _check(lib().pso_init_part(inst.h, C.byref(params), seed, first_swarm, st, C.byref(h)),
+                   "pso_init_part")
         self.h = h
+
+    def swarm_bests(self):
+        """(costs m int64, permutations m x n int32) of the swarm bests P^G."""
+        m = self.params.swarms
+        costs = np.zeros(m, np.int64)
+        perms = np.zeros((m, self.n), np.int32)
+        _check(lib().pso_swarm_bests(self.h, _ptr(costs), _ptr(perms)), "pso_swarm_bests")
+        return costs, perms
+
+    def set_swarm_best(self, swarm, cost, perm):
+        perm = np.ascontiguousarray(perm, np.int32)
+        _check(lib().pso_set_swarm_best(self.h, swarm, int(cost), _ptr(perm)), "pso_set_swarm_best")
+
+    def particle(self, index):
+        """(cost, permutation) of particle `index` (swarm-major within the state)."""
+        c = C.c_int64()
+        perm = np.zeros(self.n, np.int32)
+        _check(lib().pso_particle(self.h, index, C.byref(c), _ptr(perm)), "pso_particle")
+        return c.value, perm
 
     def step(self, iterations=1):
         _check(lib().pso_step(self.h, iterations), "pso_step")
@@ -332,6 +375,38 @@ class Swarm:
         out = np.zeros(bins + 2, np.int64)
         _check(lib().pso_cost_histogram(self.h, swarm, lo, hi, bins, _ptr(out)), "pso_cost_histogram")
         return out
+
+    def trace_start(self, capacity, lo, hi, bins):
+        """Record the statistics of every following iteration on the device."""
+        _check(lib().pso_trace_start(self.h, capacity, lo, hi, bins), "pso_trace_start")
+
+    def trace_read(self, max_records=None):
+        """The recorded iterations, oldest first: a list of dicts with t, the population
+        statistics, per-swarm statistics (m x 7: min, p5, p25, p50, p75, max, mean) and
+        the histogram."""
+        ln = C.c_int32()
+        _check(lib().pso_trace_record_len(self.h, C.byref(ln)), "pso_trace_record_len")
+        cap = max_records if max_records is not None else 1 << 16
+        buf = np.zeros((cap, ln.value), np.int64)
+        cnt = C.c_int32()
+        _check(lib().pso_trace_read(self.h, _ptr(buf), cap, C.byref(cnt)), "pso_trace_read")
+        m = self.params.swarms
+        out = []
+        for r in buf[: cnt.value]:
+            def block(w, count):
+                total = (int(w[7]) << 64) | (int(w[6]) & 0xFFFFFFFFFFFFFFFF)
+                q, rem = int(total // count), int(total % count)
+                if total < 0 and rem:  # truncated quotient, as the C side divides
+                    q, rem = q + 1, rem - count
+                return dict(min=int(w[0]), p5=int(w[1]), p25=int(w[2]), p50=int(w[3]), p75=int(w[4]),
+                            max=int(w[5]), mean=float(q) + float(rem) / count, sum=total)
+            out.append(dict(t=int(r[0]), population=block(r[1:9], self.P),
+                            swarms=[block(r[9 + 8 * k: 17 + 8 * k], self.params.swarm_size) for k in range(m)],
+                            histogram=r[9 + 8 * m:].copy()))
+        return out
+
+    def trace_stop(self):
+        _check(lib().pso_trace_stop(self.h), "pso_trace_stop")
 
     def export_state(self):
         n, P, m = self.n, self.P, self.params.swarms

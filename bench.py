@@ -40,8 +40,8 @@ def workload_config(storage="fp32"):
             "l2": ("V (168 MB fp32) is larger than L2: timed iterations back to back"
                    if storage == "fp32" else "L2 flushed (256 MiB write) before every timed iteration"),
             "timing": "value: K iterations replayed from the captured CUDA graphs, CUDA events on the "
-                      "state's stream; kernel_ms_per_step: 30 further iterations launched kernel by "
-                      "kernel with events around each, L2 flushed before each"}
+                      "state's stream; kernel_ms_per_step: min(K, 30) further iterations launched kernel "
+                      "by kernel with events around each, L2 flushed before each"}
 
 
 def params(Q, storage):
@@ -107,7 +107,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one launch of each kernel on this workload, from one
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum); set to None
 # when the kernel changes
-PROFILED_TRAFFIC = {"cost_ls": None, "position_sx": None, "velocity": None}
+PROFILED_TRAFFIC = {"cost_ls": None, "update": None}
 STEADY_FROM = 200      # the steady window starts after this many iterations
 FULL_ITERS = 300       # iterations of the whole configuration
 QUALITY_SEEDS = 8      # seeds of the fp32 / bf16 whole runs
@@ -126,13 +126,12 @@ def aggregate(units, span_s, dist, torch, device):
 
 
 def algorithmic(n, dmoves, drounds, particles, swarms, storage_bytes):
-    """Algorithmic work of one iteration: velocity bytes (V read and written, X and P^L
-    read, P^G once per swarm), position bytes (V read, X read, S_x result written),
-    local-search integer ops (below; dmoves = accepted moves in the iteration) and the
-    set-up product's tensor flops (2 n^3 per particle)."""
+    """Algorithmic work of one iteration: the update's bytes (V read and written once,
+    X and P^L read, the S_x result written, P^G once per swarm), local-search integer
+    ops (below; dmoves = accepted moves in the iteration) and the set-up product's
+    tensor flops (2 n^3 per particle)."""
     npairs = n * (n - 1) // 2
-    vel_bytes = particles * (2 * n * n * storage_bytes + 2 * n) + swarms * n
-    pos_bytes = particles * (n * n * storage_bytes + 2 * n)
+    upd_bytes = particles * (2 * n * n * storage_bytes + 3 * n) + swarms * n
     # integer ops of the goal function and a swap local search with a Delta table
     # (symmetric form): n(n-1)/2 for the cost, 3 (n-2) per pair for the table, and per
     # accepted move 3 (n-2) per pair touching the swapped positions plus 7 per other pair
@@ -140,7 +139,7 @@ def algorithmic(n, dmoves, drounds, particles, swarms, storage_bytes):
     ls_ops = (particles * (npairs + npairs * (n - 2) * 3)
               + dmoves * (touching * (n - 2) * 3 + (npairs - touching) * 7))
     ls_tc_flops = particles * 2 * n ** 3
-    return vel_bytes, pos_bytes, ls_ops, ls_tc_flops
+    return upd_bytes, ls_ops, ls_tc_flops
 
 
 def measure(Q, W, torch, storage, steps, warmup, rank, flush):
@@ -255,9 +254,9 @@ def run_ours(args, rank, world, local_rank):
         s2 = sw.stats()
         dmoves = s2["ls_moves"] - s1["ls_moves"]
         drounds = s2["ls_rounds"] - s1["ls_rounds"]
-        vel_bytes, pos_bytes, ls_ops, ls_flops = algorithmic(
+        upd_bytes, ls_ops, ls_flops = algorithmic(
             N, dmoves / kb, drounds / kb, SWARMS * SWARM_SIZE, SWARMS, 4 if storage == Q.V_FP32 else 2)
-        pos_ms, ls_ms, bests_ms, _, vel_ms = (m / kb for m in ms)
+        upd_ms, ls_ms, bests_ms, _, _ = (m / kb for m in ms)
         best, _, best_it = sw.best()
         # the steady window: the same population advanced (untimed) past STEADY_FROM
         # iterations, where the swarms have converged and S_x meets many equal maxima
@@ -276,19 +275,18 @@ def run_ours(args, rank, world, local_rank):
             pit4 = s4["particle_iterations"] - s3["particle_iterations"]
             steady = {"from_iteration": s3["iteration"], "iterations": k_st,
                       "value": SWARMS * SWARM_SIZE * k_st / st_span, "ms_per_step": st_span * 1e3 / k_st,
-                      "kernel_ms_per_step": {"velocity": ms_st[4] / 10, "position_sx": ms_st[0] / 10,
-                                             "cost_ls": ms_st[1] / 10, "bests_migration": ms_st[2] / 10},
+                      "kernel_ms_per_step": {"update": ms_st[0] / 10, "cost_ls": ms_st[1] / 10,
+                                             "bests_migration": ms_st[2] / 10},
                       "sx_ties_per_particle": (s4["sx_ties"] - s3["sx_ties"]) / pit4,
                       "moves_per_particle": (s5["ls_moves"] - s4["ls_moves"]) / (10 * SWARMS * SWARM_SIZE)}
         results[storage_name] = dict(
             value=pits / span, ms_per_step=span * 1e3 / args.steps,
             delta_evals_per_s=(dfull + dincr) * world / span,
             delta_full_per_s=dfull * world / span, delta_incr_per_s=dincr * world / span,
-            kernel_ms={"velocity": vel_ms, "position_sx": pos_ms, "cost_ls": ls_ms,
-                       "bests_migration": bests_ms},
-            vel_gbs=vel_bytes / (vel_ms / 1e3) / 1e9, pos_gbs=pos_bytes / (pos_ms / 1e3) / 1e9,
+            kernel_ms={"update": upd_ms, "cost_ls": ls_ms, "bests_migration": bests_ms},
+            upd_gbs=upd_bytes / (upd_ms / 1e3) / 1e9,
             ls_tops=ls_ops / (ls_ms / 1e3) / 1e12, ls_tc_tflops=ls_flops / (ls_ms / 1e3) / 1e12,
-            vel_bytes=vel_bytes, pos_bytes=pos_bytes, ls_ops=ls_ops,
+            upd_bytes=upd_bytes, ls_ops=ls_ops,
             moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * kb), flush_each=flush_each,
             breakdown_iterations=kb,
             best_cost=best, best_iter=best_it, iterations=args.warmup + args.steps,
@@ -384,14 +382,12 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src
                                     "subtract and multiply one op: n(n-1)/2 for the cost, 3(n-2) per "
                                     "pair for the table, per accepted move 3(n-2) per pair touching "
                                     "the swapped positions and 7 per other pair"},
-            "position_sx": {"kernel": "k_position (SecondTarget, Algorithm 1)", "bound": "hbm",
-                            "achieved": r["pos_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                            "frac": r["pos_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["position_sx"],
-                            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
-            "velocity": {"kernel": "k_velocity (Eq. 4 + S_v)", "bound": "hbm",
-                         "achieved": r["vel_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                         "frac": r["vel_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["velocity"],
-                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "update": {"kernel": "k_update (Eq. 4 + S_v, Eq. 5 with SecondTarget, Algorithm 1)",
+                       "bound": "hbm", "achieved": r["upd_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                       "frac": r["upd_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["update"],
+                       "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                       "bytes": "V read and written once (2 n^2 x 4 B), X and P^L read, S_x result "
+                                "written (3 n B) per particle, P^G once per swarm"},
         }
         roof = roofs[max(roofs, key=lambda k: km[k])]  # the kernel that takes longest
         line = {
@@ -406,11 +402,11 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src
             "roofline_all": roofs,
             "ls_setup_tensor_tflops": r["ls_tc_tflops"],
             "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
-                                                       "kernel_ms", "vel_gbs", "best_cost", "steady")}
+                                                       "kernel_ms", "upd_gbs", "best_cost", "steady")}
                      if "bf16" in results else None),
             "moves_per_particle_iteration": r["moves_per_pit"],
             "steady": r["steady"],
-            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": r["clocks"],
+            "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
         return line
@@ -523,8 +519,7 @@ def run_batch(args, quick=False):
                                      "team2 (n<=64)": sum(32 < n <= 64 for n in ns),
                                      "team8 (n<=128)": sum(64 < n <= 128 for n in ns),
                                      "simt (n>128)": sum(n > 128 for n in ns)}},
-           "kernel_ms_per_step": {"velocity": ms[4] / kb, "position_sx": ms[0] / kb,
-                                  "cost_ls": ms[1] / kb, "bests_migration": ms[2] / kb},
+           "kernel_ms_per_step": {"update": ms[0] / kb, "cost_ls": ms[1] / kb, "bests_migration": ms[2] / kb},
            "timing": "value: graph replays of the whole batch, CUDA events; kernel_ms_per_step: "
                      "further iterations launched kernel by kernel, L2 flushed before each",
            "clocks": clk.summary(), "gpu_launches": None}

@@ -140,10 +140,11 @@ int pso_step(pso_state_t st, int32_t iterations);
 
 /* Like pso_step, but launches each kernel of every iteration directly (no graph)
  * with CUDA events around it on the state's stream, then synchronises. Adds into
- * ms_out[0..4] the device milliseconds of (0) the position update S_x, (1) goal
- * function + local search, (2) bests + migration, (4) the velocity update, summed
- * over the iterations, and (3) the sum of each iteration's span from its first
- * kernel's start to its last kernel's end.
+ * ms_out[0..4] the device milliseconds of (0) the particle update (velocity, Eq. 4,
+ * and position, Eq. 5 with S_x: one kernel), (1) goal function + local search,
+ * (2) bests + migration, summed over the iterations, (3) the sum of each
+ * iteration's span from its first kernel's start to its last kernel's end, and
+ * (4) nothing (0; the velocity has no kernel of its own).
  * If flush_buf (device, flush_bytes long) is not NULL it is overwritten before every
  * iteration, outside the timed spans, to evict the L2 cache. For measurement. */
 int pso_step_timed(pso_state_t st, int32_t iterations, void* flush_buf, size_t flush_bytes,

@@ -100,8 +100,8 @@ cudaError_t autotune(pso_batch* b) {
         for (int w : {1, 2, 4}) {
             VsxLaunch L = b->vsx;
             L.warps = w;
-            if (launch_position(L, b->stream) != cudaSuccess) continue;  // warm
-            const float ms = time_on(b->stream, 2, [&] { launch_position(L, b->stream); });
+            if (launch_velocity_sx(L, b->stream) != cudaSuccess) continue;  // warm
+            const float ms = time_on(b->stream, 2, [&] { launch_velocity_sx(L, b->stream); });
             if (ms < best) {
                 best = ms;
                 pick = w;
@@ -225,10 +225,8 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
         e = cudaMemcpy(d_args, g.host.data(), sizeof(LsArgs) * g.host.size(), cudaMemcpyHostToDevice);
         b->groups.push_back(g);
     }
-    int any_old = 0, any_new = 0;
-    for (int i = 0; i < count; ++i) (params[i].pos_uses_new_v ? any_new : any_old) = 1;
-    b->vsx = VsxLaunch{b->d_views, b->d_prefix, count, n_max, total,
-                       params[0].v_storage == PSO_V_BF16, 0, any_old, any_new, d_pos_work};
+    b->vsx = VsxLaunch{b->d_views, b->d_prefix, count, n_max, total, params[0].v_storage == PSO_V_BF16, 0,
+                       d_pos_work};
     if (e == cudaSuccess && autotune_shapes) {
         e = autotune(b);
         // the tuning runs advanced the members: start them again from their seeds

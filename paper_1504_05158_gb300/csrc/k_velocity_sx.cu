@@ -103,13 +103,15 @@ __global__ void k_init(StateView s) {
 // rows holding it (a bit mask over the rows, in shared memory). The X(t) cell itself,
 // Y[pz][c] = V[pz][c] + 1, is kept apart, so ignoring it (the first `depth` steps) or
 // losing it (row pz assigned) never forces a rescan. A deleted row leaves every
-// mask, so a cache whose rows have all gone keeps its value as an upper bound
-// (count 0) and is rescanned only when needed; +inf means never scanned, -inf means
-// no rows left. Deleted rows are bits of `dead` (shared memory, one word per 32
-// rows). The scan reads 32 rows at a time with independent loads.
+// mask; once the rows holding the maximum have all gone, the cache keeps the
+// largest value the scan saw below the maximum as an upper bound of the remaining
+// rows (count 0) and is rescanned only when that bound could matter; +inf means never
+// scanned, -inf means no rows left. Deleted rows are bits of `dead` (shared memory,
+// one word per 32 rows). The scan reads 32 rows at a time with independent loads.
 struct ColMax {
     float v;
     int cnt;
+    float v2;  // the largest value below v over the scanned rows (-inf if none)
 };
 
 // The maximum of column c over the remaining rows other than pz; em (the column's
@@ -117,7 +119,7 @@ struct ColMax {
 template <typename VT>
 __device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz, uint32_t* em) {
     const float kNegInf = __int_as_float(0xff800000);
-    ColMax r{kNegInf, 0};
+    ColMax r{kNegInf, 0, kNegInf};
     for (int base = 0, wi = 0; base < n; base += 32, ++wi) {
         uint32_t ok = ~dead[wi];
         if ((pz >> 5) == wi) ok &= ~(1u << (pz & 31));
@@ -131,18 +133,26 @@ __device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n
 #pragma unroll
         for (int b = 1; b < 32; ++b) mx = fmaxf(mx, v[b]);
         uint32_t eq = 0u;
+        float sm = kNegInf;  // the largest value of the word below its maximum
 #pragma unroll
-        for (int b = 0; b < 32; ++b) eq |= (((ok >> b) & 1u) && v[b] == mx) ? (1u << b) : 0u;
+        for (int b = 0; b < 32; ++b) {
+            eq |= (((ok >> b) & 1u) && v[b] == mx) ? (1u << b) : 0u;
+            sm = fmaxf(sm, v[b] < mx ? v[b] : kNegInf);
+        }
         uint32_t keep = 0u;
         if (eq) {
             if (r.cnt == 0 || mx > r.v) {
                 for (int k = 0; k < wi; ++k) em[32 * k] = 0u;  // a larger maximum: earlier rows leave
+                r.v2 = fmaxf(fmaxf(r.cnt ? r.v : kNegInf, r.v2), sm);
                 r.v = mx;
                 r.cnt = __popc(eq);
                 keep = eq;
             } else if (mx == r.v) {
                 r.cnt += __popc(eq);
+                r.v2 = fmaxf(r.v2, sm);
                 keep = eq;
+            } else {
+                r.v2 = fmaxf(r.v2, mx);
             }
         }
         em[32 * wi] = keep;
@@ -370,7 +380,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
     __syncwarp();
     // word wi of column slot w's row mask
     auto emw = [&](int w, int wi) -> uint32_t& { return em[(w * nwr + wi) * 32 + lane]; };
-    float zv[NW], vm[NW];
+    float zv[NW], vm[NW], v2[NW];
     int vc[NW];
     bool alive[NW], zal[NW], ex[NW];
 #pragma unroll
@@ -381,6 +391,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         ex[w] = false;
         zv[w] = alive[w] ? VStore<VT>::to_f(tile[pic[w] * n + c]) + zadd : 0.0f;
         vm[w] = __int_as_float(0x7f800000);
+        v2[w] = vm[w];
         vc[w] = 0;
         newp[w] = 0;
     }
@@ -440,6 +451,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                     const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
                     vm[w] = cm.v;
                     vc[w] = cm.cnt;
+                    v2[w] = cm.v2;
                 }
             uint32_t lp = 0u;
 #pragma unroll
@@ -511,6 +523,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                         cnt += __popc(mv & ~gone[wi]);
                     }
                     vc[w] = cnt;
+                    if (cnt == 0) vm[w] = v2[w];  // the maximum's rows are gone: the bound below it
                 }
                 step += nb;
                 continue;
@@ -532,6 +545,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                 const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
                 vm[w] = cm.v;
                 vc[w] = cm.cnt;
+                v2[w] = cm.v2;
             }
             float e;
             if (vc[w] == 0) {  // the X(t) cell above a stale bound, or nothing else left
@@ -698,7 +712,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                 const uint32_t bit = 1u << (r & 31), mv = m;
                 if (mv & bit) {
                     m = mv & ~bit;
-                    --vc[w];
+                    if (--vc[w] == 0) vm[w] = v2[w];  // the maximum's rows are gone: the bound below it
                 }
             }
         }
@@ -717,300 +731,80 @@ struct TableCursor {
     }
 };
 
-// Velocity (Eq. 4 + S_v) of every particle of the table whose position update uses
-// V(t+1) (phase 1) or V(t) (phase 0). One CTA of kVelWarps warps per particle: one
-// thread brings the tile of the CTA's next particle into shared memory with a bulk
-// copy while the warps update the current one (two buffers), so several tiles are
-// in flight per SM and V is read from memory once. Warp w takes rows w, w +
-// kVelWarps, ... of the lane's columns j = lane + 32 c; Norm adds the warps' partial
-// column sums in shared memory in a fixed order; V(t+1) is stored from registers.
-constexpr int kVelWarps = 8;
-
+// Velocity (Eq. 4 + S_v) of one particle in its shared-memory tile, in place, by one
+// warp: lane `lane` owns the columns j = lane + 32 c. W = clamp(c1 v) everywhere but
+// at the rows X(t), P^L and P^G of a column (at most three), where the attraction
+// terms enter; those cells are formed from exact splits and rounded once (eq4_cell),
+// so they keep their relative accuracy when the terms cancel. Norm divides column j
+// by the sum of |W| over the column (four interleaved partial sums, added pairwise);
+// a zero column stays zero.
 template <int NW, typename VT>
-__global__ void __launch_bounds__(kVelWarps * 32)
-    k_velocity(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int phase,
-               int n_max) {
-    constexpr int R = (32 * NW + kVelWarps - 1) / kVelWarps;  // rows per warp for n <= 32 NW
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ float part[kVelWarps][32 * NW];
-    __shared__ float inv_s[32 * NW];
-    __shared__ Split ab_s[2][2];  // c2 r2 and c3 r3 (exact splits) of the particle of each buffer
-    __shared__ __align__(8) uint64_t bar[2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-    const size_t tb_max = tile_bytes<VT>(n_max);
-    const int total = prefix[count];
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-    }
-    __syncthreads();
-    TableCursor look;
-    auto next_active = [&](int f) {  // the CTA's next particle of this phase
-        for (; f < total; f += gridDim.x) {
-            look.advance(prefix, count, f);
-            const StateView& v = views[look.inst];
-            if (((v.pos_uses_new_v != 0) == (phase != 0)) && !v.sx_only) break;
-        }
-        return f;
-    };
-    auto issue = [&](int f, int slot) {  // thread 0: the bulk load of particle f's tile
-        const StateView& v = views[look.inst];
-        fence_proxy_async();
-        bulk_load(smem + (size_t)slot * tb_max,
-                  reinterpret_cast<const VT*>(v.V) + (size_t)(f - prefix[look.inst]) * v.vstride,
-                  (uint32_t)tile_bytes<VT>(v.n), bar + slot);
-    };
-    int f = next_active(blockIdx.x);
-    if (f < total && tid == 0) issue(f, 0);
-    uint32_t par0 = 0u, par1 = 0u;
-    int slot = 0;
-    TableCursor cur;
-    // thread 0: the updated tile of the previous particle, stored by one bulk copy
-    // once every warp has written it (after the next CTA barrier)
-    VT* pend_dst = nullptr;
-    uint32_t pend_bytes = 0;
-    while (f < total) {
-        const int p = cur.advance(prefix, count, f);
-        const StateView s = views[cur.inst];
-        const int fn = next_active(f + gridDim.x);
-        const int n = s.n;
-        const uint32_t t = (uint32_t)*s.t;
-        const int lsw = p / s.ss;  // the swarm in this population; draws use its index in the run
-        const uint32_t swarm = (uint32_t)(s.swarm_base + lsw), pis = (uint32_t)(p % s.ss);
-        int pic[NW], plc[NW], pgc[NW];
+__device__ __noinline__ void velocity_in_tile(VT* tile, int n, int lane, const uint8_t* xrow, const uint8_t* plrow,
+                                              const uint8_t* pgrow, float c1, float vmax, bool norm, Split a,
+                                              Split b) {
+    auto wgen = [&](float v) { return fminf(fmaxf(__fmul_rn(c1, v), -vmax), vmax); };
 #pragma unroll
-        for (int c = 0; c < NW; ++c) {
-            const int j = lane + 32 * c;
-            pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
-            plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[c] = j < n ? s.PG[(size_t)lsw * s.ps + j] : -1;
-        }
-        if (tid == 0) {  // one draw per particle, shared through shared memory
-            const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-            ab_s[slot][0] = exact_mul(s.c2, u01f(ur.x));
-            ab_s[slot][1] = exact_mul(s.c3, u01f(ur.y));
-        }
-        const bool norm = s.sv_kind == 1;
-        // one warp waits for the tile; the CTA barrier passes it on (and orders every
-        // warp's reads of the other buffer, from the previous particle, before its refill)
-        bool landed = true;
-        const uint32_t par = slot ? par1 : par0;
-        if (warp == 0) landed = mbar_wait(bar + slot, par);
-        const bool ok = __syncthreads_and(landed);
-        const Split a = ab_s[slot][0], b = ab_s[slot][1];
-        if (slot)
-            par1 ^= 1u;
-        else
-            par0 ^= 1u;
-        if (!ok) {  // the copy did not land in time: record, stop this CTA
-            if (tid == 0) {
-                atomicAdd(s.counters + CNT_ERR, 1ull);
-                // the load may still be in flight into this CTA's shared memory: give it
-                // one more bounded wait before the CTA exits, and let the stores finish
-                mbar_wait(bar + slot, par);
-                bulk_wait_all();
-            }
-            return;
-        }
-        if (tid == 0) {
-            if (pend_dst) {
-                fence_proxy_async();
-                bulk_store(pend_dst, smem + (size_t)(slot ^ 1) * tb_max, pend_bytes);
-                pend_dst = nullptr;
-            }
-            if (fn < total) {
-                bulk_wait_read();  // the store has read the buffer the next tile goes to
-                issue(fn, slot ^ 1);
+    for (int c = 0; c < NW; ++c) {
+        const int j = lane + 32 * c;
+        if (j >= n) continue;
+        const int px = xrow[j], pl = plrow[j], pg = pgrow[j];
+        // the distinct special rows of the column and their values from V(t)
+        int srow[3];
+        float sval[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            int i = q == 0 ? px : (q == 1 ? pl : pg);
+            if (q >= 1 && i == px) i = -1;
+            if (q == 2 && i == pl) i = -1;
+            srow[q] = i;
+            sval[q] = 0.0f;
+            if (i >= 0) {
+                const int dl = (pl == i) - (px == i);
+                const int dg = (pg == i) - (px == i);
+                const float v = VStore<VT>::to_f(tile[i * n + j]);
+                sval[q] = fminf(fmaxf(eq4_cell(exact_mul(c1, v), a, b, dl, dg), -vmax), vmax);
             }
         }
-        VT* tile = reinterpret_cast<VT*>(smem + (size_t)slot * tb_max);
-        // W at a cell: c1 v + a dl + b dg, clamped; dl and dg vanish outside the rows
-        // X(t), P^L and P^G of the column, where W is clamp(c1 v). At those rows the
-        // terms can cancel, so W is formed from exact splits and rounded once (eq4_cell);
-        // with dl = dg = 0 that gives the same fp32 value as c1 v
-        auto wgen = [&](float v) { return fminf(fmaxf(__fmul_rn(s.c1, v), -s.v_max), s.v_max); };
-        auto wval = [&](int i, int c) {
-            const float v = VStore<VT>::to_f(tile[i * n + lane + 32 * c]);
-            const int dl = (plc[c] == i) - (pic[c] == i);
-            const int dg = (pgc[c] == i) - (pic[c] == i);
-            return fminf(fmaxf(eq4_cell(exact_mul(s.c1, v), a, b, dl, dg), -s.v_max), s.v_max);
-        };
-        // the distinct special rows of column c owned by this warp: row i of the tile
-        // belongs to warp i mod kVelWarps
-        auto special = [&](int c, int q) {  // q = 0, 1, 2: X(t), P^L, P^G row, or -1
-            const int i = q == 0 ? pic[c] : (q == 1 ? plc[c] : pgc[c]);
-            if (i < 0 || i % kVelWarps != warp) return -1;
-            if (q >= 1 && i == pic[c]) return -1;
-            if (q == 2 && i == plc[c]) return -1;
-            return i;
-        };
+        float inv = 1.0f;
         if (norm) {
-            float sum[NW];
-#pragma unroll
-            for (int c = 0; c < NW; ++c) sum[c] = 0.0f;
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const int i = warp + kVelWarps * u;
-#pragma unroll
-                for (int c = 0; c < NW; ++c)
-                    if (i < n && lane + 32 * c < n) sum[c] += fabsf(wgen(VStore<VT>::to_f(tile[i * n + lane + 32 * c])));
+            float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+            int i = 0;
+            for (; i + 3 < n; i += 4) {
+                p0 += fabsf(wgen(VStore<VT>::to_f(tile[i * n + j])));
+                p1 += fabsf(wgen(VStore<VT>::to_f(tile[(i + 1) * n + j])));
+                p2 += fabsf(wgen(VStore<VT>::to_f(tile[(i + 2) * n + j])));
+                p3 += fabsf(wgen(VStore<VT>::to_f(tile[(i + 3) * n + j])));
             }
+            for (; i < n; ++i) p0 += fabsf(wgen(VStore<VT>::to_f(tile[i * n + j])));
+            float sum = (p0 + p1) + (p2 + p3);
 #pragma unroll
-            for (int c = 0; c < NW; ++c) {
-                if (lane + 32 * c >= n) continue;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const int i = special(c, q);
-                    if (i >= 0)
-                        sum[c] += fabsf(wval(i, c)) - fabsf(wgen(VStore<VT>::to_f(tile[i * n + lane + 32 * c])));
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < NW; ++c) part[warp][lane + 32 * c] = sum[c];
-            __syncthreads();
-            for (int j = tid; j < 32 * NW; j += blockDim.x) {
-                float tsum = 0.0f;
-#pragma unroll
-                for (int w = 0; w < kVelWarps; ++w) tsum += part[w][j];
-                inv_s[j] = tsum > 0.0f ? 1.0f / tsum : 1.0f;
-            }
-            __syncthreads();
+            for (int q = 0; q < 3; ++q)
+                if (srow[q] >= 0) sum += fabsf(sval[q]) - fabsf(wgen(VStore<VT>::to_f(tile[srow[q] * n + j])));
+            inv = sum > 0.0f ? 1.0f / sum : 1.0f;
         }
-        // V(t+1) into the tile in place: the special rows from V(t) first, then every
-        // row with the generic value, then the special rows again
-#pragma unroll
-        for (int c = 0; c < NW; ++c) {
-            const int j = lane + 32 * c;
-            if (j >= n) continue;
-            const float iv = norm ? inv_s[j] : 1.0f;
-            float sx[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int i = special(c, q);
-                sx[q] = i >= 0 ? wval(i, c) : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const int i = warp + kVelWarps * u;
-                if (i < n) {
-                    const float x = wgen(VStore<VT>::to_f(tile[i * n + j]));
-                    tile[i * n + j] = VStore<VT>::from_f(norm ? x * iv : x);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int i = special(c, q);
-                if (i >= 0) tile[i * n + j] = VStore<VT>::from_f(norm ? sx[q] * iv : sx[q]);
-            }
+        for (int i = 0; i < n; ++i) {
+            const float x = wgen(VStore<VT>::to_f(tile[i * n + j]));
+            tile[i * n + j] = VStore<VT>::from_f(norm ? x * inv : x);
         }
-        fence_proxy_async();  // this thread's tile writes, before the bulk store reads them
-        if (tid == 0) {
-            pend_dst = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
-            pend_bytes = (uint32_t)tile_bytes<VT>(n);
-        }
-        slot ^= 1;  // the next particle's barrier frees this tile, part and inv_s
-        f = fn;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (pend_dst) bulk_store(pend_dst, smem + (size_t)(slot ^ 1) * tb_max, pend_bytes);
-        bulk_wait_all();
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (srow[q] >= 0) tile[srow[q] * n + j] = VStore<VT>::from_f(norm ? sval[q] * inv : sval[q]);
     }
 }
 
-// The same for n > 128: one warp per particle, rows streamed in batches of RB whose
-// loads are issued before any use; Norm reads the rows twice (the second read
-// mostly hits L2).
-template <int NW, typename VT>
-__global__ void __launch_bounds__(128)
-    k_velocity_wide(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count,
-                    int phase) {
-    constexpr int RB = 2;
-    const int wpc = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int total = prefix[count];
-    TableCursor cur;
-    for (int f = blockIdx.x * wpc + warp; f < total; f += gridDim.x * wpc) {
-        const int p = cur.advance(prefix, count, f);
-        const StateView s = views[cur.inst];
-        if ((s.pos_uses_new_v != 0) != (phase != 0) || s.sx_only) continue;
-        const int n = s.n;
-        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
-        const uint32_t t = (uint32_t)*s.t;
-        const int lsw = p / s.ss;  // the swarm in this population; draws use its index in the run
-        const uint32_t swarm = (uint32_t)(s.swarm_base + lsw), pis = (uint32_t)(p % s.ss);
-        int pic[NW], plc[NW], pgc[NW];
-#pragma unroll
-        for (int c = 0; c < NW; ++c) {
-            const int j = lane + 32 * c;
-            pic[c] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
-            plc[c] = j < n ? s.PL[(size_t)p * s.ps + j] : -1;
-            pgc[c] = j < n ? s.PG[(size_t)lsw * s.ps + j] : -1;
-        }
-        const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);
-        const Split a = exact_mul(s.c2, u01f(ur.x)), b = exact_mul(s.c3, u01f(ur.y));
-        const bool norm = s.sv_kind == 1;
-        auto wval = [&](int i, int c, float x0) {
-            const int dl = (plc[c] == i) - (pic[c] == i);
-            const int dg = (pgc[c] == i) - (pic[c] == i);
-            const float w = (dl | dg) ? eq4_cell(exact_mul(s.c1, x0), a, b, dl, dg) : __fmul_rn(s.c1, x0);
-            return fminf(fmaxf(w, -s.v_max), s.v_max);
-        };
-        float inv[NW];
-#pragma unroll
-        for (int c = 0; c < NW; ++c) inv[c] = 1.0f;
-        if (norm) {
-            float sum[NW];
-#pragma unroll
-            for (int c = 0; c < NW; ++c) sum[c] = 0.0f;
-            for (int i0 = 0; i0 < n; i0 += RB) {
-                float v[RB][NW];
-#pragma unroll
-                for (int u = 0; u < RB; ++u)
-#pragma unroll
-                    for (int c = 0; c < NW; ++c) {
-                        const int i = i0 + u, j = lane + 32 * c;
-                        v[u][c] = (i < n && j < n) ? VStore<VT>::to_f(Vg[i * n + j]) : 0.0f;
-                    }
-#pragma unroll
-                for (int u = 0; u < RB; ++u)
-#pragma unroll
-                    for (int c = 0; c < NW; ++c)
-                        if (i0 + u < n && lane + 32 * c < n) sum[c] += fabsf(wval(i0 + u, c, v[u][c]));
-            }
-#pragma unroll
-            for (int c = 0; c < NW; ++c) inv[c] = sum[c] > 0.0f ? 1.0f / sum[c] : 1.0f;
-        }
-        for (int i0 = 0; i0 < n; i0 += RB) {
-            float v[RB][NW];
-#pragma unroll
-            for (int u = 0; u < RB; ++u)
-#pragma unroll
-                for (int c = 0; c < NW; ++c) {
-                    const int i = i0 + u, j = lane + 32 * c;
-                    v[u][c] = (i < n && j < n) ? VStore<VT>::to_f(Vg[i * n + j]) : 0.0f;
-                }
-#pragma unroll
-            for (int u = 0; u < RB; ++u)
-#pragma unroll
-                for (int c = 0; c < NW; ++c) {
-                    const int i = i0 + u, j = lane + 32 * c;
-                    if (i < n && j < n) {
-                        const float x = wval(i, c, v[u][c]);
-                        Vg[i * n + j] = VStore<VT>::from_f(norm ? x * inv[c] : x);
-                    }
-                }
-        }
-    }
-}
-
-// Position (Eq. 5, S_x = SecondTarget) of every particle of the table: the V tile
-// (V(t), or V(t+1) already written by the velocity kernel) is staged in shared memory
-// with one bulk copy; shared-memory slots are sized for the largest n of the table.
+// One particle iteration's update of every particle of the table, one warp per
+// particle: the V tile is staged in shared memory with one bulk copy; S_x
+// (SecondTarget, Algorithm 1, or PickColumn) runs on Y = X(t) + V(t) and the velocity
+// of Eq. 4 replaces the tile in place (the other order when the population forms
+// X(t) + V(t+1)); one bulk copy stores V(t+1). V is read from memory once and written
+// once per iteration. Shared-memory slots are sized for the largest n of the table;
+// particles are handed out one at a time from a counter (their cost varies with the
+// ties of the greedy), else in a fixed grid-stride order. The discretisation entry
+// point (sx_only) runs S_x alone on Y.
 template <int NW, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
-    k_position(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
-               int32_t* __restrict__ work) {
+    k_update(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
+             int32_t* __restrict__ work) {
     const int wpc = blockDim.x >> 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1026,8 +820,6 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int total = prefix[count];
     TableCursor cur;
 
-    // particles are handed out one at a time from a counter (their cost varies with
-    // the ties of the greedy), else in a fixed grid-stride order
     auto grab = [&](int fixed) {
         if (!work) return fixed;
         int q = 0;
@@ -1041,12 +833,15 @@ __global__ void __launch_bounds__(kWarps * 32)
         const uint32_t t = (uint32_t)*s.t;
         const uint32_t tbytes = (uint32_t)tile_bytes<VT>(n);
         const bool sx_only = s.sx_only != 0;
-        const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(s.swarm_base + p / s.ss);
+        const int lsw = p / s.ss;  // the swarm in this population; draws use its index in the run
+        const uint32_t swarm = sx_only ? (uint32_t)s.sx_swarm[p] : (uint32_t)(s.swarm_base + lsw);
         const uint32_t pis = sx_only ? (uint32_t)s.sx_pis[p] : (uint32_t)(p % s.ss);
-        const VT* Vg = reinterpret_cast<const VT*>(s.V) + (size_t)p * s.vstride;
-        // the tile -> shared memory with one bulk copy (tile padded to 16 bytes)
+        VT* Vg = reinterpret_cast<VT*>(s.V) + (size_t)p * s.vstride;
+        // the tile -> shared memory with one bulk copy (tile padded to 16 bytes), once
+        // the store of the previous particle has finished reading it
         __syncwarp();
         if (lane == 0) {
+            bulk_wait_read();
             fence_proxy_async();
             bulk_load(tile, Vg, tbytes, bar);
         }
@@ -1057,15 +852,29 @@ __global__ void __launch_bounds__(kWarps * 32)
             pic[w] = j < n ? s.X[(size_t)p * s.ps + j] : -1;
             newp[w] = 0;
         }
+        // the velocity's inputs are loaded when it runs, so that nothing of it stays
+        // live across S_x
+        auto velocity = [&]() {
+            const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);  // r2, r3: one draw per particle
+            velocity_in_tile<NW, VT>(tile, n, lane, s.X + (size_t)p * s.ps, s.PL + (size_t)p * s.ps,
+                                     s.PG + (size_t)lsw * s.ps, s.c1, s.v_max, s.sv_kind == 1,
+                                     exact_mul(s.c2, u01f(ur.x)), exact_mul(s.c3, u01f(ur.y)));
+        };
         const bool ok = mbar_wait(bar, phase);
         if (!__all_sync(FULL, ok)) {  // the copy did not land in time: record, leave this warp
             if (lane == 0) {
                 atomicAdd(s.counters + CNT_ERR, 1ull);
                 mbar_wait(bar, phase);  // one more bounded wait for a load still in flight
+                bulk_wait_all();
             }
             return;
         }
         phase ^= 1u;
+        const bool new_v = !sx_only && s.pos_uses_new_v != 0;
+        if (new_v) {  // X(t) + V(t+1): the velocity first
+            velocity();
+            __syncwarp();
+        }
         // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
         // the discretisation entry point
         const float zadd = sx_only ? 0.0f : 1.0f;
@@ -1080,21 +889,29 @@ __global__ void __launch_bounds__(kWarps * 32)
             if (j < n) s.Xsx[(size_t)p * s.ps + j] = (uint8_t)newp[w];
         }
         if (lane == 0 && ties) atomicAdd(s.counters + CNT_TIES, (unsigned long long)ties);
+        if (!sx_only) {
+            __syncwarp();  // S_x has read the tile
+            if (!new_v) velocity();
+            fence_proxy_async();  // this lane's tile writes, before the bulk store reads them
+            __syncwarp();
+            if (lane == 0) bulk_store(Vg, tile, tbytes);
+        }
         __syncwarp();
     }
+    if (lane == 0) bulk_wait_all();
 }
 
 template <int NW, typename VT>
-cudaError_t launch_pos(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_upd(const VsxLaunch& L, cudaStream_t st) {
     int wpc = L.warps > 0 ? L.warps : kWarps;  // warps (particles) per CTA
     if (wpc > kWarps) wpc = kWarps;
     while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(L.n_max) > kSmemLimit) --wpc;
     const size_t smem = kBarBytes + wpc * warp_bytes<VT>(L.n_max);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = configure_once<k_position<NW, VT>>();
+    cudaError_t e = configure_once<k_update<NW, VT>>();
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
-    int per_sm = occupancy_cached<k_position<NW, VT>>(wpc * 32, smem);
+    int per_sm = occupancy_cached<k_update<NW, VT>>(wpc * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     const int need = (L.total + wpc - 1) / wpc;
@@ -1104,62 +921,21 @@ cudaError_t launch_pos(const VsxLaunch& L, cudaStream_t st) {
         e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
     }
-    k_position<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work);
-    return cudaGetLastError();
-}
-
-template <int NW, typename VT>
-cudaError_t launch_vel(const VsxLaunch& L, int phase, cudaStream_t st) {
-    const int sms = sm_count();
-    int per_sm = 0;
-    if constexpr (NW <= 4) {
-        const size_t smem = 2 * tile_bytes<VT>(L.n_max);
-        if (smem > kSmemLimit - 8 * 1024) return cudaErrorInvalidValue;
-        cudaError_t e = configure_once<k_velocity<NW, VT>>();
-        if (e != cudaSuccess) return e;
-        per_sm = occupancy_cached<k_velocity<NW, VT>>(kVelWarps * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        int grid = sms * per_sm;
-        if (grid > L.total) grid = L.total;
-        k_velocity<NW, VT><<<grid, kVelWarps * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, phase, L.n_max);
-    } else {
-        constexpr int kWide = 4;
-        per_sm = occupancy_cached<k_velocity_wide<NW, VT>>(kWide * 32, 0);
-        if (per_sm < 1) per_sm = 1;
-        int grid = sms * per_sm;
-        const int need = (L.total + kWide - 1) / kWide;
-        if (grid > need) grid = need;
-        k_velocity_wide<NW, VT><<<grid, kWide * 32, 0, st>>>(L.d_views, L.d_prefix, L.count, phase);
-    }
+    k_update<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t launch_pos_t(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_upd_t(const VsxLaunch& L, cudaStream_t st) {
     switch ((L.n_max + 31) / 32) {
-        case 1: return launch_pos<1, VT>(L, st);
-        case 2: return launch_pos<2, VT>(L, st);
-        case 3: return launch_pos<3, VT>(L, st);
-        case 4: return launch_pos<4, VT>(L, st);
-        case 5: return launch_pos<5, VT>(L, st);
+        case 1: return launch_upd<1, VT>(L, st);
+        case 2: return launch_upd<2, VT>(L, st);
+        case 3: return launch_upd<3, VT>(L, st);
+        case 4: return launch_upd<4, VT>(L, st);
+        case 5: return launch_upd<5, VT>(L, st);
         case 6:
         case 7:
-        case 8: return launch_pos<8, VT>(L, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename VT>
-cudaError_t launch_vel_t(const VsxLaunch& L, int phase, cudaStream_t st) {
-    switch ((L.n_max + 31) / 32) {
-        case 1: return launch_vel<1, VT>(L, phase, st);
-        case 2: return launch_vel<2, VT>(L, phase, st);
-        case 3: return launch_vel<3, VT>(L, phase, st);
-        case 4: return launch_vel<4, VT>(L, phase, st);
-        case 5: return launch_vel<5, VT>(L, phase, st);
-        case 6: return launch_vel<6, VT>(L, phase, st);
-        case 7: return launch_vel<7, VT>(L, phase, st);
-        case 8: return launch_vel<8, VT>(L, phase, st);
+        case 8: return launch_upd<8, VT>(L, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1187,23 +963,10 @@ cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_position(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
     if (L.total <= 0) return cudaSuccess;
     if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
-    return L.v_bf16 ? launch_pos_t<__nv_bfloat16>(L, st) : launch_pos_t<float>(L, st);
-}
-
-cudaError_t launch_velocity(const VsxLaunch& L, int phase, cudaStream_t st) {
-    if (L.total <= 0 || !(phase ? L.has_new_v : L.has_old_v)) return cudaSuccess;
-    if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
-    return L.v_bf16 ? launch_vel_t<__nv_bfloat16>(L, phase, st) : launch_vel_t<float>(L, phase, st);
-}
-
-cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
-    cudaError_t e = launch_velocity(L, 1, st);
-    if (e == cudaSuccess) e = launch_position(L, st);
-    if (e == cudaSuccess) e = launch_velocity(L, 0, st);
-    return e;
+    return L.v_bf16 ? launch_upd_t<__nv_bfloat16>(L, st) : launch_upd_t<float>(L, st);
 }
 
 }  // namespace qap

@@ -72,8 +72,9 @@ cudaError_t launch_ls(const LsLaunch& L, cudaStream_t st);
 // largest n a search kernel serves
 int ls_max_n(LsKind kind);
 
-// The velocity and position launches over `count` populations (flat index over
-// particles).
+// The update of every particle of `count` populations (flat index over particles):
+// velocity (Eq. 4 + S_v) and position (Eq. 5, S_x) in one kernel, one warp per
+// particle, V read and written once.
 struct VsxLaunch {
     const StateView* d_views;
     const int32_t* d_prefix;  // count + 1 particle offsets
@@ -81,17 +82,10 @@ struct VsxLaunch {
     int n_max;
     int total;                // prefix[count]
     int v_bf16;               // every population of the table has the same storage
-    int warps;                // warps per CTA of the position kernel (0 = automatic)
-    int has_old_v;            // some population forms X(t) + V(t) (velocity after S_x)
-    int has_new_v;            // some population forms X(t) + V(t+1) (velocity first)
-    int32_t* d_work;          // the position kernel's particle counter (zeroed before
-                              // each launch), or null for a fixed grid-stride order
+    int warps;                // warps per CTA (0 = automatic)
+    int32_t* d_work;          // the kernel's particle counter (zeroed before each
+                              // launch), or null for a fixed grid-stride order
 };
-// S_x of every particle (reads the V tiles, writes Xsx)
-cudaError_t launch_position(const VsxLaunch& L, cudaStream_t st);
-// Eq. 4 for the populations of the phase (1: pos_uses_new_v, 0: the others)
-cudaError_t launch_velocity(const VsxLaunch& L, int phase, cudaStream_t st);
-// velocity (phase 1), position, velocity (phase 0): one iteration's update
 cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st);
 int velocity_sx_max_n(int v_bf16);
 

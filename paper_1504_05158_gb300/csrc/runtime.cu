@@ -103,7 +103,7 @@ cudaError_t reinit_state(pso_state* s, cudaStream_t st) {
 cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
                              const TimedParts& T, float* ms_out) {
     if (iterations <= 0) return cudaSuccess;
-    constexpr int E = 6;  // [vel(new V)] pos [vel(old V)] search bests
+    constexpr int E = 4;  // update (velocity + S_x), search, bests
     std::vector<cudaEvent_t> ev((size_t)iterations * E, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto& x : ev)
@@ -112,16 +112,12 @@ cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, s
         cudaEvent_t* q = &ev[(size_t)i * E];
         if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, st);
         if (e == cudaSuccess) e = cudaEventRecord(q[0], st);
-        if (e == cudaSuccess) e = launch_velocity(*T.vsx, 1, st);
+        if (e == cudaSuccess) e = launch_velocity_sx(*T.vsx, st);
         if (e == cudaSuccess) e = cudaEventRecord(q[1], st);
-        if (e == cudaSuccess) e = launch_position(*T.vsx, st);
-        if (e == cudaSuccess) e = cudaEventRecord(q[2], st);
-        if (e == cudaSuccess) e = launch_velocity(*T.vsx, 0, st);
-        if (e == cudaSuccess) e = cudaEventRecord(q[3], st);
         for (int g = 0; g < T.nls && e == cudaSuccess; ++g) e = launch_ls(T.ls[g], st);
-        if (e == cudaSuccess) e = cudaEventRecord(q[4], st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[2], st);
         if (e == cudaSuccess) e = launch_bests(T.views, T.count, T.m_max, 0, st);
-        if (e == cudaSuccess) e = cudaEventRecord(q[5], st);
+        if (e == cudaSuccess) e = cudaEventRecord(q[3], st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -131,11 +127,10 @@ cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, s
         return ms;
     };
     for (int i = 0; i < iterations && e == cudaSuccess; ++i) {
-        acc[0] += span(i, 1, 2);
-        acc[1] += span(i, 3, 4);
-        acc[2] += span(i, 4, 5);
-        acc[3] += span(i, 0, 5);
-        acc[4] += span(i, 0, 1) + span(i, 2, 3);
+        acc[0] += span(i, 0, 1);
+        acc[1] += span(i, 1, 2);
+        acc[2] += span(i, 2, 3);
+        acc[3] += span(i, 0, 3);
     }
     for (auto& x : ev)
         if (x) cudaEventDestroy(x);
@@ -414,8 +409,7 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->h_ls[1] = ls_args_for(s, true, s->d_work + 1);
     s->h_prefix[0] = 0;
     s->h_prefix[1] = P;
-    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0,
-                       params->pos_uses_new_v ? 0 : 1, params->pos_uses_new_v ? 1 : 0, s->d_work + 2};
+    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0, s->d_work + 2};
     s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     e = cudaMemsetAsync(base, 0, off, s->stream);
@@ -943,9 +937,9 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     up(oPre, prefix, sizeof(prefix));
     if (e == cudaSuccess) e = cudaMemset(base + oC, 0, CNT_N * 8);
     if (e == cudaSuccess)
-        e = launch_position(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
-                                      count, 0, 0, 0, 0},
-                            0);
+        e = launch_velocity_sx(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
+                                         count, 0, 0, nullptr},
+                               0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     unsigned long long cnt[CNT_N] = {};
     if (e == cudaSuccess) e = cudaMemcpy(cnt, base + oC, sizeof(cnt), cudaMemcpyDeviceToHost);

@@ -59,8 +59,8 @@ struct TimedParts {
 };
 // Runs `iterations` iterations with events around every phase (after writing
 // flush_bytes of flush_buf, when given) and adds the device milliseconds to ms_out:
-// [0] position (S_x), [1] goal function + local search, [2] bests + migration,
-// [3] whole iterations, [4] velocity.
+// [0] the update (velocity and S_x, one kernel), [1] goal function + local search,
+// [2] bests + migration, [3] whole iterations, [4] 0 (kept for the layout).
 cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
                              const TimedParts& T, float* ms_out);
 int status_of(cudaError_t e);

@@ -258,6 +258,20 @@ def run_ours(args, rank, world, local_rank):
             N, dmoves / kb, drounds / kb, SWARMS * SWARM_SIZE, SWARMS, 4 if storage == Q.V_FP32 else 2)
         upd_ms, ls_ms, bests_ms, _, _ = (m / kb for m in ms)
         best, _, best_it = sw.best()
+        # the search kernels side by side on this iteration's S_x results (the same
+        # permutations): tensor-core set-up, int32 SIMT set-up, int64 SIMT set-up, direct
+        search_kernels = None
+        if storage == Q.V_FP32 and not args.no_extras and world == 1:
+            xs = sw.export_state()["X_sx"]
+            gi2 = Q.Instance(W.grid64().F, W.grid64().D)
+            search_kernels = {}
+            for kname, kk in (("tensor", Q.SEARCH_TENSOR), ("simt", Q.SEARCH_SIMT), ("int64", Q.SEARCH_INT64),
+                              ("direct", Q.SEARCH_DIRECT)):
+                _, _, mv, _, kms = gi2.search_with(kk, xs, 0, timed=True)
+                _, ops, _ = algorithmic(N, int(mv.sum()), 0, len(xs), SWARMS, 4)
+                search_kernels[kname] = {"ms": kms, "moves": int(mv.sum()),
+                                         "tops": ops / (kms / 1e3) / 1e12}
+            gi2.close()
         # the steady window: the same population advanced (untimed) past STEADY_FROM
         # iterations, where the swarms have converged and S_x meets many equal maxima
         steady = None
@@ -290,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
             moves_per_pit=dmoves / (SWARMS * SWARM_SIZE * kb), flush_each=flush_each,
             breakdown_iterations=kb,
             best_cost=best, best_iter=best_it, iterations=args.warmup + args.steps,
-            clocks=clk.summary(), steady=steady)
+            clocks=clk.summary(), steady=steady, search_kernels=search_kernels)
         sw.close()
 
     # the whole configuration (300 iterations) over several seeds, fp32 and bf16: the
@@ -401,6 +415,8 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src
             "roofline": roof,
             "roofline_all": roofs,
             "ls_setup_tensor_tflops": r["ls_tc_tflops"],
+            "search_kernels": ({k: dict(v, frac=v["tops"] / alu_peak_tops) for k, v in r["search_kernels"].items()}
+                               if r.get("search_kernels") else None),
             "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
                                                        "kernel_ms", "upd_gbs", "best_cost", "steady")}
                      if "bf16" in results else None),
@@ -569,6 +585,50 @@ def run_serve(args, quick=False):
     print(json.dumps(out))
 
 
+def run_table1(args):
+    """The configuration space of section 4.1, Table 1 (inertia c1 in {0.5, 0.8},
+    c2 = c3 in {0.3, 0.5}, Raw or Norm velocity kernel, migration factor 0 or 33 %:
+    Algorithm 2 with d = floor(0.33 m) every iteration) on synthetic instances shaped
+    like the table's rows (QAPLIB is not available): dense uniform n = 26 and n = 60,
+    and the n = 64 grid instance; 200 swarms x 50 particles, args.table1_iters
+    iterations each. One JSON line: best cost, iteration found, median final cost and
+    particle-iterations/s per setting."""
+    import itertools
+
+    import torch
+
+    from paper_1504_05158_gb300 import build as B
+    B.build()
+    from paper_1504_05158_gb300 import qap_pso as Q
+    from paper_1504_05158_gb300 import workloads as W
+    insts = {"dense26": W.dense_uniform(26, 26), "dense60": W.dense_uniform(60, 60), "grid64": W.grid64()}
+    m, ss, iters = 200, 50, args.table1_iters
+    rows = []
+    stream = torch.cuda.Stream()
+    for name, inst in insts.items():
+        gi = Q.Instance(inst.F, inst.D)
+        for c1, c23, sv, mig in itertools.product((0.5, 0.8), (0.3, 0.5), (Q.SV_RAW, Q.SV_NORM), (0.0, 0.33)):
+            prm = Q.default_params(swarms=m, swarm_size=ss, c1=c1, c2=c23, c3=c23, sv_kind=sv,
+                                   mig_kind=Q.MIG_RANK if mig else Q.MIG_NONE, mig_depth=int(mig * m),
+                                   mig_period=1)
+            sw = Q.Swarm(gi, prm, seed=2015, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            span = timed_steps(sw, torch, stream, iters, None, False)
+            best, _, it = sw.best()
+            st = sw.stats()
+            rows.append({"instance": name, "n": inst.n, "c1": c1, "c2": c23, "c3": c23,
+                         "velocity": "Raw" if sv == Q.SV_RAW else "Norm", "migration": mig,
+                         "best": best, "iteration": it, "final_p50": st["p50"],
+                         "value": m * ss * iters / span})
+            sw.close()
+        gi.close()
+    print(json.dumps({"metric": "Table 1 configuration space on synthetic instances", "unit": UNIT,
+                      "config": {"swarms": m, "swarm_size": ss, "iterations": iters, "seed": 2015,
+                                 "sx": "SecondTarget depth 2 (Algorithm 1)", "v_max": 1.0,
+                                 "local_search": "full swap search every iteration"},
+                      "data": "synthetic", "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,9 +644,11 @@ def main():
                     help="seconds of arrivals of the serving summary on the main line")
     ap.add_argument("--variants", default="fp32,bf16",
                     help="velocity storage formats to time (fp32 is the headline)")
-    ap.add_argument("--workload", choices=("grid64", "batch64", "serve"), default="grid64",
+    ap.add_argument("--workload", choices=("grid64", "batch64", "serve", "table1"), default="grid64",
                     help="grid64: the headline n = 64 workload; batch64 / serve: the batch and "
-                         "serving workloads (separate JSON lines)")
+                         "serving workloads; table1: the configuration sweep of section 4.1 "
+                         "(separate JSON lines)")
+    ap.add_argument("--table1-iters", type=int, default=100)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--serve-iters", type=int, default=150)
@@ -604,6 +666,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -341,12 +341,14 @@ int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t
  *   QAP_SEARCH_INT64   int64 arithmetic (the int64 SIMT set-up for symmetric
  *                      instances that fit it, else the direct kernel);
  *   QAP_SEARCH_DIRECT  every swap value from the general O(n) formula, int64.
- * Errors: QAP_ERR_UNSUPPORTED when the named kernel is not exact for the instance
- * or does not serve its n; QAP_ERR_OVERFLOW, QAP_ERR_INVALID_ARG as above. */
+ * kernel_ms (host, may be NULL) receives the device time of the kernel launch
+ * (CUDA events around it). Errors: QAP_ERR_UNSUPPORTED when the named kernel is not
+ * exact for the instance or does not serve its n; QAP_ERR_OVERFLOW,
+ * QAP_ERR_INVALID_ARG as above. */
 enum { QAP_SEARCH_AUTO = 0, QAP_SEARCH_TENSOR = 1, QAP_SEARCH_SIMT = 2, QAP_SEARCH_INT64 = 3,
        QAP_SEARCH_DIRECT = 4 };
 int qap_search_with(qap_instance_t inst, int32_t kernel, int32_t* perms, int32_t count, int32_t max_moves,
-                    int64_t* costs, int32_t* moves, int32_t* rounds);
+                    int64_t* costs, int32_t* moves, int32_t* rounds, float* kernel_ms);
 
 /* Swap values of one permutation: out[idx(r, s)] = f(p o (r s)) - f(p) for every
  * pair r < s, in r-major order (idx = r n - r (r + 1) / 2 + s - r - 1), by the

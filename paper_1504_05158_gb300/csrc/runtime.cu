@@ -295,13 +295,17 @@ int pso_init_part(qap_instance_t inst, const pso_params_t* params, uint64_t seed
 static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t seed, int32_t first_swarm,
                       bool part, void* stream, pso_state_t* out) {
     if (!inst || !params || !out || first_swarm < 0) return QAP_ERR_INVALID_ARG;
-    int v = validate(inst, params);
+    pso_params_t prm = *params;
+    if (part) {  // a part of a run: the caller migrates (the run's migration depth may exceed the part's)
+        prm.mig_kind = PSO_MIG_NONE;
+        prm.mig_depth = 0;
+    }
+    int v = validate(inst, &prm);
     if (v != QAP_OK) return v;
     pso_state* s = new (std::nothrow) pso_state();
     if (!s) return QAP_ERR_OOM;
     s->inst = inst;
-    s->prm = *params;
-    if (part) s->prm.mig_kind = PSO_MIG_NONE;  // a part of a run: the caller migrates
+    s->prm = prm;
     params = &s->prm;
     s->seed = seed;
     if (stream) {
@@ -708,7 +712,7 @@ int pso_import_state(pso_state_t s, const pso_host_state_t* in) {
 }
 
 static int run_ls_hook(qap_instance_t inst, int force, const int32_t* perms, int32_t count, int32_t max_moves,
-                       int32_t* perms_out, int64_t* costs, int32_t* moves, int32_t* rounds) {
+                       int32_t* perms_out, int64_t* costs, int32_t* moves, int32_t* rounds, float* kernel_ms) {
     const int n = inst->n;
     for (int c = 0; c < count; ++c) {
         std::vector<char> seen(n, 0);
@@ -756,8 +760,16 @@ static int run_ls_hook(qap_instance_t inst, int force, const int32_t* perms, int
         LsArgs* da = nullptr;
         e = cudaMalloc(&da, sizeof(LsArgs));
         if (e == cudaSuccess) e = cudaMemcpy(da, &a, sizeof(LsArgs), cudaMemcpyHostToDevice);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (e == cudaSuccess && kernel_ms) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess && kernel_ms) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess && kernel_ms) e = cudaEventRecord(e0, 0);
         if (e == cudaSuccess) e = launch_ls(LsLaunch{da, dw, 1, n, (int)kind, 0, count}, 0);
+        if (e == cudaSuccess && kernel_ms) e = cudaEventRecord(e1, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && kernel_ms) e = cudaEventElapsedTime(kernel_ms, e0, e1);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
         cudaFree(da);
     }
     std::vector<int64_t> hc(count);
@@ -814,17 +826,18 @@ static int forced_kind(const qap_instance* inst, int32_t kernel, int* out) {
 }
 
 int qap_eval_costs(qap_instance_t inst, const int32_t* perms, int32_t count, int64_t* out) {
-    return qap_search_with(inst, QAP_SEARCH_AUTO, const_cast<int32_t*>(perms), count, -1, out, nullptr, nullptr);
+    return qap_search_with(inst, QAP_SEARCH_AUTO, const_cast<int32_t*>(perms), count, -1, out, nullptr, nullptr,
+                           nullptr);
 }
 
 int qap_local_search(qap_instance_t inst, int32_t* perms, int32_t count, int32_t max_moves,
                      int64_t* costs, int32_t* moves, int32_t* rounds) {
     if (max_moves < 0) return QAP_ERR_INVALID_ARG;
-    return qap_search_with(inst, QAP_SEARCH_AUTO, perms, count, max_moves, costs, moves, rounds);
+    return qap_search_with(inst, QAP_SEARCH_AUTO, perms, count, max_moves, costs, moves, rounds, nullptr);
 }
 
 int qap_search_with(qap_instance_t inst, int32_t kernel, int32_t* perms, int32_t count, int32_t max_moves,
-                    int64_t* costs, int32_t* moves, int32_t* rounds) {
+                    int64_t* costs, int32_t* moves, int32_t* rounds, float* kernel_ms) {
     if (!inst || !perms || count < 0) return QAP_ERR_INVALID_ARG;
     if (max_moves < 0 && !costs) return QAP_ERR_INVALID_ARG;
     if (!inst->exact64) return QAP_ERR_OVERFLOW;
@@ -833,7 +846,7 @@ int qap_search_with(qap_instance_t inst, int32_t kernel, int32_t* perms, int32_t
     if (st != QAP_OK) return st;
     if (count == 0) return QAP_OK;
     return run_ls_hook(inst, force, perms, count, max_moves, max_moves < 0 ? nullptr : perms, costs, moves,
-                       rounds);
+                       rounds, kernel_ms);
 }
 
 int qap_delta_table(qap_instance_t inst, const int32_t* perm, int64_t* out) {

@@ -117,7 +117,7 @@ def lib():
         L.pso_import_state.argtypes = [vp, C.POINTER(HostState)]
         L.qap_eval_costs.argtypes = [vp, vp, C.c_int32, vp]
         L.qap_local_search.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp]
-        L.qap_search_with.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.qap_search_with.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, vp, C.POINTER(C.c_float)]
         L.qap_int32_peak.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pso_trace_start.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.c_int32]
         L.pso_trace_record_len.argtypes = [vp, C.POINTER(C.c_int32)]
@@ -243,17 +243,19 @@ class Instance:
                                       _ptr(rounds)), "qap_local_search")
         return perms, costs, moves, rounds
 
-    def search_with(self, kernel, perms, max_moves=0):
+    def search_with(self, kernel, perms, max_moves=0, timed=False):
         """The goal function (max_moves < 0) or the local search on the named search
-        kernel (SEARCH_*); returns (perms, costs, moves, rounds)."""
+        kernel (SEARCH_*); returns (perms, costs, moves, rounds), plus the kernel's
+        device milliseconds when timed."""
         perms = np.ascontiguousarray(perms, np.int32).reshape(-1, self.n).copy()
         k = len(perms)
         costs = np.zeros(k, np.int64)
         moves = np.zeros(k, np.int32)
         rounds = np.zeros(k, np.int32)
+        ms = C.c_float()
         _check(lib().qap_search_with(self.h, kernel, _ptr(perms), k, max_moves, _ptr(costs), _ptr(moves),
-                                     _ptr(rounds)), "qap_search_with")
-        return perms, costs, moves, rounds
+                                     _ptr(rounds), C.byref(ms) if timed else None), "qap_search_with")
+        return (perms, costs, moves, rounds, ms.value) if timed else (perms, costs, moves, rounds)
 
     def delta_table(self, perm):
         """Delta(r, s) of every pair r < s of `perm`, r-major (n (n - 1) / 2 int64)."""

@@ -472,8 +472,22 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                 // is the first of its value group when no equal cell of the round sits
                 // in a lower column (same register slot: lower lane; lower slot: any lane)
                 int mine = 0, firsts = 0;
+                // a round whose cells all hold one value (the converged swarm: every X(t)
+                // cell of Y is 0.5) has one distinct value; no comparison across lanes needed
+                uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
+#pragma unroll
+                for (int w = 0; w < NW; ++w)
+                    if (inB[w]) {
+                        kmin = min(kmin, bkey[w]);
+                        kmax = max(kmax, bkey[w]);
+                    }
+                const bool one_value = __reduce_min_sync(FULL, kmin) == __reduce_max_sync(FULL, kmax);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
+                    if (one_value) {
+                        mine += inB[w] ? 1 : 0;
+                        continue;
+                    }
                     const unsigned grp = __match_any_sync(FULL, inB[w] ? bkey[w] : 0xFFFFFFFFu);
                     bool first = inB[w] && (__ffs(grp) - 1 == lane);
 #pragma unroll
@@ -487,7 +501,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                     firsts += first ? 1 : 0;
                 }
                 const int nb = (int)__reduce_add_sync(FULL, (unsigned)mine);
-                const int distinct = (int)__reduce_add_sync(FULL, (unsigned)firsts);
+                const int distinct = one_value ? 1 : (int)__reduce_add_sync(FULL, (unsigned)firsts);
                 ties += nb - distinct;
                 // assign, delete the rows, and let the other columns lose them
                 uint32_t gone[NW];
@@ -792,6 +806,120 @@ __device__ __noinline__ void velocity_in_tile(VT* tile, int n, int lane, const u
     }
 }
 
+// Two adjacent columns per lane (n even): the same velocity as velocity_in_tile with
+// 8-byte (fp32) or 4-byte (bf16) shared-memory accesses; lane `lane` owns columns
+// 2 lane + 64 c and 2 lane + 64 c + 1. Column sums from four interleaved partial sums
+// (rows mod 4, added pairwise); the write pass loads four rows before it stores them.
+template <typename VT>
+struct Pair;
+template <>
+struct Pair<float> {
+    static __device__ __forceinline__ void get(const float* p, float& a, float& b) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void put(float* p, float a, float b) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ void get(const __nv_bfloat16* p, float& a, float& b) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+        a = __low2float(v);
+        b = __high2float(v);
+    }
+    static __device__ __forceinline__ void put(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+template <typename VT>
+__device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uint8_t* xrow, const uint8_t* plrow,
+                                            const uint8_t* pgrow, float c1, float vmax, bool norm, Split a,
+                                            Split b) {
+    auto wgen = [&](float v) { return fminf(fmaxf(__fmul_rn(c1, v), -vmax), vmax); };
+    for (int j0 = 2 * lane; j0 < n; j0 += 64) {
+        int srow[2][3];
+        float sval[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + h;
+            const int px = xrow[j], pl = plrow[j], pg = pgrow[j];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                int i = q == 0 ? px : (q == 1 ? pl : pg);
+                if (q >= 1 && i == px) i = -1;
+                if (q == 2 && i == pl) i = -1;
+                srow[h][q] = i;
+                sval[h][q] = 0.0f;
+                if (i >= 0) {
+                    const int dl = (pl == i) - (px == i);
+                    const int dg = (pg == i) - (px == i);
+                    const float v = VStore<VT>::to_f(tile[i * n + j]);
+                    sval[h][q] = fminf(fmaxf(eq4_cell(exact_mul(c1, v), a, b, dl, dg), -vmax), vmax);
+                }
+            }
+        }
+        float inv0 = 1.0f, inv1 = 1.0f;
+        if (norm) {
+            float px[4] = {0.f, 0.f, 0.f, 0.f}, py[4] = {0.f, 0.f, 0.f, 0.f};
+            int i = 0;
+            for (; i + 3 < n; i += 4) {
+                float x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) Pair<VT>::get(tile + (i + u) * n + j0, x[u], y[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    px[u] += fabsf(wgen(x[u]));
+                    py[u] += fabsf(wgen(y[u]));
+                }
+            }
+            for (; i < n; ++i) {
+                float x0, y0;
+                Pair<VT>::get(tile + i * n + j0, x0, y0);
+                px[0] += fabsf(wgen(x0));
+                py[0] += fabsf(wgen(y0));
+            }
+            float s0 = (px[0] + px[1]) + (px[2] + px[3]), s1 = (py[0] + py[1]) + (py[2] + py[3]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (srow[0][q] >= 0)
+                    s0 += fabsf(sval[0][q]) - fabsf(wgen(VStore<VT>::to_f(tile[srow[0][q] * n + j0])));
+                if (srow[1][q] >= 0)
+                    s1 += fabsf(sval[1][q]) - fabsf(wgen(VStore<VT>::to_f(tile[srow[1][q] * n + j0 + 1])));
+            }
+            inv0 = s0 > 0.0f ? 1.0f / s0 : 1.0f;
+            inv1 = s1 > 0.0f ? 1.0f / s1 : 1.0f;
+        }
+        int i = 0;
+        for (; i + 3 < n; i += 4) {
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) Pair<VT>::get(tile + (i + u) * n + j0, x[u], y[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float gx = wgen(x[u]), gy = wgen(y[u]);
+                Pair<VT>::put(tile + (i + u) * n + j0, norm ? gx * inv0 : gx, norm ? gy * inv1 : gy);
+            }
+        }
+        for (; i < n; ++i) {
+            float x, y;
+            Pair<VT>::get(tile + i * n + j0, x, y);
+            x = wgen(x);
+            y = wgen(y);
+            Pair<VT>::put(tile + i * n + j0, norm ? x * inv0 : x, norm ? y * inv1 : y);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (srow[0][q] >= 0) tile[srow[0][q] * n + j0] = VStore<VT>::from_f(norm ? sval[0][q] * inv0 : sval[0][q]);
+            if (srow[1][q] >= 0)
+                tile[srow[1][q] * n + j0 + 1] = VStore<VT>::from_f(norm ? sval[1][q] * inv1 : sval[1][q]);
+        }
+    }
+}
+
 // One particle iteration's update of every particle of the table, one warp per
 // particle: the V tile is staged in shared memory with one bulk copy; S_x
 // (SecondTarget, Algorithm 1, or PickColumn) runs on Y = X(t) + V(t) and the velocity
@@ -856,9 +984,13 @@ __global__ void __launch_bounds__(kWarps * 32)
         // live across S_x
         auto velocity = [&]() {
             const U4 ur = draw(s.seed, pis, swarm, t, TAG_R, 0u);  // r2, r3: one draw per particle
-            velocity_in_tile<NW, VT>(tile, n, lane, s.X + (size_t)p * s.ps, s.PL + (size_t)p * s.ps,
-                                     s.PG + (size_t)lsw * s.ps, s.c1, s.v_max, s.sv_kind == 1,
-                                     exact_mul(s.c2, u01f(ur.x)), exact_mul(s.c3, u01f(ur.y)));
+            const Split a = exact_mul(s.c2, u01f(ur.x)), b = exact_mul(s.c3, u01f(ur.y));
+            if ((n & 1) == 0)  // rows start on 8 (fp32) or 4 (bf16) bytes: paired columns
+                velocity_pairs<VT>(tile, n, lane, s.X + (size_t)p * s.ps, s.PL + (size_t)p * s.ps,
+                                   s.PG + (size_t)lsw * s.ps, s.c1, s.v_max, s.sv_kind == 1, a, b);
+            else
+                velocity_in_tile<NW, VT>(tile, n, lane, s.X + (size_t)p * s.ps, s.PL + (size_t)p * s.ps,
+                                         s.PG + (size_t)lsw * s.ps, s.c1, s.v_max, s.sv_kind == 1, a, b);
         };
         const bool ok = mbar_wait(bar, phase);
         if (!__all_sync(FULL, ok)) {  // the copy did not land in time: record, leave this warp

@@ -26,6 +26,7 @@ namespace qap {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kSlowSingles = 8;  // single greedy steps from which a particle goes first next time
 constexpr size_t kBarBytes = 64;  // one mbarrier per warp, ahead of the tiles
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -158,6 +159,83 @@ __device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n
         em[32 * wi] = keep;
     }
     return r;
+}
+
+// The float of an order key (fkey's inverse; +0 for the key of +-0).
+__device__ __forceinline__ float unkey(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// The cache vscan forms, for one column c whose scan the whole warp shares: lane l reads
+// rows l, l + 32, ...; the maximum and the largest value below it are warp reductions of
+// the order keys, the rows holding the maximum are ballots (bit l of word q = row
+// 32 q + l, the mask layout). Every lane receives the result; lane q writes word q of
+// the column's mask (em: the column's first word, words 32 apart). A rebuild of a few
+// columns costs a few warp-wide instructions each instead of a whole scan by one lane
+// while the others wait.
+template <int NW, typename VT>
+__device__ __forceinline__ ColMax coscan(const VT* tile, const uint32_t* dead, int n, int lane, int c, int pz,
+                                         uint32_t* em) {
+    uint32_t key[NW];
+    uint32_t lm = 0u;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int i = 32 * q + lane;
+        const bool ok = i < n && i != pz && !((dead[q] >> lane) & 1u);
+        key[q] = ok ? fkey(VStore<VT>::to_f(tile[i * n + c])) : 0u;
+        lm = max(lm, key[q]);
+    }
+    const uint32_t km = __reduce_max_sync(FULL, lm);
+    uint32_t l2 = 0u;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) l2 = max(l2, key[q] < km ? key[q] : 0u);
+    const uint32_t k2 = __reduce_max_sync(FULL, l2);
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if (32 * q >= n) continue;
+        const unsigned m = __ballot_sync(FULL, key[q] != 0u && key[q] == km);
+        cnt += __popc(m);
+        if (lane == q) em[32 * q] = m;
+    }
+    const float kNegInf = __int_as_float(0xff800000);
+    return ColMax{km ? unkey(km) : kNegInf, km ? cnt : 0, k2 ? unkey(k2) : kNegInf};
+}
+
+// Rebuilds the caches of the owned columns that need it (need[w]): by the warp together
+// (coscan) when at most kCoopMax columns of a slot need it, else by each lane alone
+// (vscan, every lane scanning its own column at once).
+constexpr int kCoopMax = 8;
+template <int NW, typename VT>
+__device__ __forceinline__ void rebuild(const VT* tile, const uint32_t* dead, uint32_t* em, int nwr, int n, int lane,
+                                        const int (&pic)[NW], const bool (&need)[NW], float (&vm)[NW],
+                                        int (&vc)[NW], float (&v2)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const unsigned who = __ballot_sync(FULL, need[w]);
+        if (!who) continue;
+        if (__popc(who) > kCoopMax) {
+            if (need[w]) {
+                const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &em[(w * nwr) * 32 + lane]);
+                vm[w] = cm.v;
+                vc[w] = cm.cnt;
+                v2[w] = cm.v2;
+            }
+            continue;
+        }
+        unsigned rem = who;
+        while (rem) {
+            const int L = __ffs(rem) - 1;
+            rem &= rem - 1u;
+            const int pz = __shfl_sync(FULL, pic[w], L);
+            const ColMax cm = coscan<NW, VT>(tile, dead, n, lane, L + 32 * w, pz, &em[(w * nwr) * 32 + L]);
+            if (lane == L) {
+                vm[w] = cm.v;
+                vc[w] = cm.cnt;
+                v2[w] = cm.v2;
+            }
+        }
+    }
 }
 
 // The last steps of SecondTarget once at most kTailCols columns are left and the
@@ -374,7 +452,8 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
 template <int NW, typename VT>
 __device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, uint32_t* em,
                                              int nwr, int n, int lane, const int (&pic)[NW], uint32_t pis,
-                                             uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW]) {
+                                             uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW],
+                                             int& singles) {
     const int depth = s.depth;
     if (lane < NW) dead[lane] = 0u;
     __syncwarp();
@@ -445,14 +524,12 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 
         if (!use_ex && try_round) {
             // ---- a round of X(t) cells above every remaining plain value ----
+            {
+                bool need[NW];
 #pragma unroll
-            for (int w = 0; w < NW; ++w)
-                if (alive[w] && !zin[w] && vc[w] == 0) {
-                    const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
-                    vm[w] = cm.v;
-                    vc[w] = cm.cnt;
-                    v2[w] = cm.v2;
-                }
+                for (int w = 0; w < NW; ++w) need[w] = alive[w] && !zin[w] && vc[w] == 0;
+                rebuild<NW, VT>(tile, dead, em, nwr, n, lane, pic, need, vm, vc, v2);
+            }
             uint32_t lp = 0u;
 #pragma unroll
             for (int w = 0; w < NW; ++w)
@@ -549,18 +626,18 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         // 2 the plain maximum alone
         uint32_t key[NW];
         int cnt[NW], mode[NW];
+        {
+            bool need[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) need[w] = alive[w] && vc[w] == 0 && !(zin[w] && zv[w] > vm[w]);
+            rebuild<NW, VT>(tile, dead, em, nwr, n, lane, pic, need, vm, vc, v2);
+        }
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             key[w] = 0u;
             cnt[w] = 0;
             mode[w] = 0;
             if (!alive[w]) continue;
-            if (vc[w] == 0 && !(zin[w] && zv[w] > vm[w])) {
-                const ColMax cm = vscan<VT>(tile, dead, n, lane + 32 * w, pic[w], &emw(w, 0));
-                vm[w] = cm.v;
-                vc[w] = cm.cnt;
-                v2[w] = cm.v2;
-            }
             float e;
             if (vc[w] == 0) {  // the X(t) cell above a stale bound, or nothing else left
                 if (!zin[w]) continue;
@@ -714,6 +791,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
             return ties;
         }
+        ++singles;
         __syncwarp();
         // the other columns lose row r
 #pragma unroll
@@ -740,6 +818,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 struct TableCursor {
     int inst = 0;
     __device__ __forceinline__ int advance(const int32_t* prefix, int count, int f) {
+        if (f < prefix[inst]) inst = 0;  // particles handed out out of order (slow ones first)
         while (inst + 1 < count && prefix[inst + 1] <= f) ++inst;
         return f - prefix[inst];
     }
@@ -932,7 +1011,7 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
 template <int NW, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
     k_update(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
-             int32_t* __restrict__ work) {
+             int32_t* __restrict__ work, SlowOrder order) {
     const int wpc = blockDim.x >> 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -948,11 +1027,20 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int total = prefix[count];
     TableCursor cur;
 
+    // the particles that took many single greedy steps in the previous iteration
+    // (order.cur_list, flagged in order.cur_flag) come first: a long particle started
+    // last would leave the other SMs idle; then every other particle, skipping those
+    const int nslow = order.cur_cnt ? *order.cur_cnt : 0;
     auto grab = [&](int fixed) {
         if (!work) return fixed;
-        int q = 0;
-        if (lane == 0) q = atomicAdd(work, 1);
-        return __shfl_sync(FULL, q, 0);
+        for (;;) {
+            int q = 0;
+            if (lane == 0) q = atomicAdd(work, 1);
+            q = __shfl_sync(FULL, q, 0);
+            if (q < nslow) return order.cur_list[q];
+            const int f = q - nslow;
+            if (f >= total || !order.cur_flag || !order.cur_flag[f]) return f;
+        }
     };
     for (int f = grab(blockIdx.x * wpc + warp); f < total; f = grab(f + gridDim.x * wpc)) {
         const int p = cur.advance(prefix, count, f);
@@ -1010,11 +1098,17 @@ __global__ void __launch_bounds__(kWarps * 32)
         // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
         // the discretisation entry point
         const float zadd = sx_only ? 0.0f : 1.0f;
+        int singles = 0;
         const int ties = s.sx_kind == 1
                              ? pick_column<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic,
                                                    pis, swarm, t, zadd, newp)
                              : second_target<NW, VT>(s, tile, dead, em, nwr, n, lane, pic, pis, swarm, t, zadd,
-                                                     newp);
+                                                     newp, singles);
+        if (order.nxt_flag && lane == 0) {  // the order of the next iteration
+            const bool slow = singles >= kSlowSingles;
+            order.nxt_flag[f] = slow ? 1 : 0;
+            if (slow) order.nxt_list[atomicAdd(order.nxt_cnt, 1)] = f;
+        }
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;
@@ -1034,7 +1128,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 }
 
 template <int NW, typename VT>
-cudaError_t launch_upd(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_upd(const VsxLaunch& L, int parity, cudaStream_t st) {
     int wpc = L.warps > 0 ? L.warps : kWarps;  // warps (particles) per CTA
     if (wpc > kWarps) wpc = kWarps;
     while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(L.n_max) > kSmemLimit) --wpc;
@@ -1053,21 +1147,33 @@ cudaError_t launch_upd(const VsxLaunch& L, cudaStream_t st) {
         e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
     }
-    k_update<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work);
+    SlowOrder order{};
+    if (L.d_work && L.order_buf) {  // parity selects which buffer is read and which written
+        const int c = parity & 1, x = c ^ 1;
+        order.cur_list = L.order_buf->list[c];
+        order.cur_cnt = L.order_buf->cnt[c];
+        order.cur_flag = L.order_buf->flag[c];
+        order.nxt_list = L.order_buf->list[x];
+        order.nxt_cnt = L.order_buf->cnt[x];
+        order.nxt_flag = L.order_buf->flag[x];
+        e = cudaMemsetAsync(order.nxt_cnt, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_update<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work, order);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t launch_upd_t(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_upd_t(const VsxLaunch& L, int parity, cudaStream_t st) {
     switch ((L.n_max + 31) / 32) {
-        case 1: return launch_upd<1, VT>(L, st);
-        case 2: return launch_upd<2, VT>(L, st);
-        case 3: return launch_upd<3, VT>(L, st);
-        case 4: return launch_upd<4, VT>(L, st);
-        case 5: return launch_upd<5, VT>(L, st);
+        case 1: return launch_upd<1, VT>(L, parity, st);
+        case 2: return launch_upd<2, VT>(L, parity, st);
+        case 3: return launch_upd<3, VT>(L, parity, st);
+        case 4: return launch_upd<4, VT>(L, parity, st);
+        case 5: return launch_upd<5, VT>(L, parity, st);
         case 6:
         case 7:
-        case 8: return launch_upd<8, VT>(L, st);
+        case 8: return launch_upd<8, VT>(L, parity, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1095,10 +1201,10 @@ cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
+cudaError_t launch_velocity_sx(const VsxLaunch& L, int parity, cudaStream_t st) {
     if (L.total <= 0) return cudaSuccess;
     if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
-    return L.v_bf16 ? launch_upd_t<__nv_bfloat16>(L, st) : launch_upd_t<float>(L, st);
+    return L.v_bf16 ? launch_upd_t<__nv_bfloat16>(L, parity, st) : launch_upd_t<float>(L, parity, st);
 }
 
 }  // namespace qap

@@ -250,9 +250,7 @@ int pso_trace_start(pso_state_t s, int32_t capacity, int64_t lo, int64_t hi, int
     s->trace.lo = lo;
     s->trace.hi = hi;
     // the captured iterations change: capture them again at the next pso_step
-    if (s->g1) cudaGraphExecDestroy(s->g1);
-    if (s->g16) cudaGraphExecDestroy(s->g16);
-    s->g1 = s->g16 = nullptr;
+    drop_graphs(s);
     return QAP_OK;
 }
 
@@ -288,9 +286,7 @@ int pso_trace_stop(pso_state_t s) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (s->trace.d) cudaFree(s->trace.d);
     s->trace = TraceBuf{};
-    if (s->g1) cudaGraphExecDestroy(s->g1);
-    if (s->g16) cudaGraphExecDestroy(s->g16);
-    s->g1 = s->g16 = nullptr;
+    drop_graphs(s);
     return status_of(e);
 }
 

@@ -41,26 +41,24 @@ struct pso_batch {
     std::vector<Group> groups;
     VsxLaunch vsx;
     int m_max;
-    cudaGraphExec_t g1[2], g16[2];  // by the parity of the first iteration they run
-    uint64_t launched;              // iterations queued so far
-    SlowOrderBuf order;             // the update kernel's particle order over the whole table
+    cudaGraphExec_t g1, g16;
 };
 
 namespace {
 
-cudaError_t enqueue(pso_batch* b, int parity) {
-    cudaError_t e = launch_velocity_sx(b->vsx, parity, b->stream);
+cudaError_t enqueue(pso_batch* b) {
+    cudaError_t e = launch_velocity_sx(b->vsx, b->stream);
     for (auto& g : b->groups)
         if (e == cudaSuccess) e = launch_ls(g.launch, b->stream);
     if (e == cudaSuccess) e = launch_bests(b->d_views, (int)b->members.size(), b->m_max, 0, b->stream);
     return e;
 }
 
-cudaError_t capture(pso_batch* b, int iters, int parity, cudaGraphExec_t* out) {
+cudaError_t capture(pso_batch* b, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < iters && e == cudaSuccess; ++i) e = enqueue(b, (parity + i) & 1);
+    for (int i = 0; i < iters && e == cudaSuccess; ++i) e = enqueue(b);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
@@ -102,8 +100,8 @@ cudaError_t autotune(pso_batch* b) {
         for (int w : {1, 2, 4}) {
             VsxLaunch L = b->vsx;
             L.warps = w;
-            if (launch_velocity_sx(L, (int)(b->launched++ & 1), b->stream) != cudaSuccess) continue;  // warm
-            const float ms = time_on(b->stream, 2, [&] { launch_velocity_sx(L, (int)(b->launched++ & 1), b->stream); });
+            if (launch_velocity_sx(L, b->stream) != cudaSuccess) continue;  // warm
+            const float ms = time_on(b->stream, 2, [&] { launch_velocity_sx(L, b->stream); });
             if (ms < best) {
                 best = ms;
                 pick = w;
@@ -188,8 +186,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     b->m_max = m_max;
     int kind_count[LS_KINDS] = {};
     for (auto* s : b->members) ++kind_count[s->ls_iter.kind];
-    size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024 + 256 +
-                   2 * ((size_t)total * 5 + 1024);
+    size_t bytes = sizeof(StateView) * count + sizeof(int32_t) * (count + 1) + 1024 + 256;
     for (int k = 0; k < LS_KINDS; ++k) bytes += (sizeof(LsArgs) + sizeof(int32_t)) * kind_count[k] + 512;
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, bytes);
@@ -207,11 +204,6 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
     b->d_views = (StateView*)take(sizeof(StateView) * count);
     b->d_prefix = (int32_t*)take(sizeof(int32_t) * (count + 1));
     int32_t* d_pos_work = (int32_t*)take(sizeof(int32_t));
-    for (int o = 0; o < 2; ++o) {
-        b->order.cnt[o] = (int32_t*)take(16);
-        b->order.list[o] = (int32_t*)take(sizeof(int32_t) * (size_t)total);
-        b->order.flag[o] = (uint8_t*)take((size_t)total);
-    }
     e = cudaMemcpy(b->d_views, b->h_views.data(), sizeof(StateView) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_prefix, b->h_prefix.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice);
@@ -234,16 +226,7 @@ int pso_batch_create(int32_t count, const qap_instance_t* insts, const pso_param
         b->groups.push_back(g);
     }
     b->vsx = VsxLaunch{b->d_views, b->d_prefix, count, n_max, total, params[0].v_storage == PSO_V_BF16, 0,
-                       d_pos_work, &b->order};
-    if (e == cudaSuccess) e = cudaMemset(base, 0, bytes);  // order buffers start empty
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_views, b->h_views.data(), sizeof(StateView) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_prefix, b->h_prefix.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice);
-    for (auto& g : b->groups)
-        if (e == cudaSuccess)
-            e = cudaMemcpy(const_cast<LsArgs*>(g.launch.d_args), g.host.data(), sizeof(LsArgs) * g.host.size(),
-                           cudaMemcpyHostToDevice);
+                       d_pos_work};
     if (e == cudaSuccess && autotune_shapes) {
         e = autotune(b);
         // the tuning runs advanced the members: start them again from their seeds
@@ -263,17 +246,16 @@ int pso_batch_step(pso_batch_t b, int32_t iterations) {
     if (!b || iterations < 0) return QAP_ERR_INVALID_ARG;
     if (iterations == 0) return QAP_OK;
     cudaError_t e = cudaSuccess;
+    if (!b->g1) e = capture(b, 1, &b->g1);
+    if (e == cudaSuccess && iterations >= 16 && !b->g16) e = capture(b, 16, &b->g16);
     int left = iterations;
+    while (left >= 16 && e == cudaSuccess) {
+        e = cudaGraphLaunch(b->g16, b->stream);
+        left -= 16;
+    }
     while (left > 0 && e == cudaSuccess) {
-        const int p = (int)(b->launched & 1);
-        const bool big = left >= 16;
-        cudaGraphExec_t* g = big ? &b->g16[p] : &b->g1[p];
-        if (!*g) e = capture(b, big ? 16 : 1, p, g);
-        if (e == cudaSuccess) e = cudaGraphLaunch(*g, b->stream);
-        if (e == cudaSuccess) {
-            b->launched += big ? 16 : 1;
-            left -= big ? 16 : 1;
-        }
+        e = cudaGraphLaunch(b->g1, b->stream);
+        --left;
     }
     return status_of(e);
 }
@@ -284,7 +266,7 @@ int pso_batch_step_timed(pso_batch_t b, int32_t iterations, void* flush_buf, siz
     std::vector<LsLaunch> ls;
     for (auto& g : b->groups) ls.push_back(g.launch);
     const TimedParts T{&b->vsx, ls.data(), (int)ls.size(), b->d_views, (int)b->members.size(), b->m_max};
-    return status_of(timed_iterations(b->stream, iterations, flush_buf, flush_bytes, T, &b->launched, ms_out));
+    return status_of(timed_iterations(b->stream, iterations, flush_buf, flush_bytes, T, ms_out));
 }
 
 int pso_batch_member(pso_batch_t b, int32_t index, pso_state_t* out) {
@@ -302,10 +284,8 @@ int pso_batch_size(pso_batch_t b, int32_t* count) {
 void pso_batch_destroy(pso_batch_t b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (int p = 0; p < 2; ++p) {
-        if (b->g1[p]) cudaGraphExecDestroy(b->g1[p]);
-        if (b->g16[p]) cudaGraphExecDestroy(b->g16[p]);
-    }
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g16) cudaGraphExecDestroy(b->g16);
     for (auto* s : b->members) pso_destroy(s);
     cudaFree(b->dbase);
     if (b->own_stream) cudaStreamDestroy(b->stream);

@@ -26,7 +26,6 @@ namespace qap {
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kSlowSingles = 8;  // single greedy steps from which a particle goes first next time
 constexpr size_t kBarBytes = 64;  // one mbarrier per warp, ahead of the tiles
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -452,8 +451,7 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
 template <int NW, typename VT>
 __device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, uint32_t* em,
                                              int nwr, int n, int lane, const int (&pic)[NW], uint32_t pis,
-                                             uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW],
-                                             int& singles) {
+                                             uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW]) {
     const int depth = s.depth;
     if (lane < NW) dead[lane] = 0u;
     __syncwarp();
@@ -791,7 +789,6 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
             return ties;
         }
-        ++singles;
         __syncwarp();
         // the other columns lose row r
 #pragma unroll
@@ -818,7 +815,6 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 struct TableCursor {
     int inst = 0;
     __device__ __forceinline__ int advance(const int32_t* prefix, int count, int f) {
-        if (f < prefix[inst]) inst = 0;  // particles handed out out of order (slow ones first)
         while (inst + 1 < count && prefix[inst + 1] <= f) ++inst;
         return f - prefix[inst];
     }
@@ -1011,7 +1007,7 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
 template <int NW, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
     k_update(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
-             int32_t* __restrict__ work, SlowOrder order) {
+             int32_t* __restrict__ work) {
     const int wpc = blockDim.x >> 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1027,20 +1023,11 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int total = prefix[count];
     TableCursor cur;
 
-    // the particles that took many single greedy steps in the previous iteration
-    // (order.cur_list, flagged in order.cur_flag) come first: a long particle started
-    // last would leave the other SMs idle; then every other particle, skipping those
-    const int nslow = order.cur_cnt ? *order.cur_cnt : 0;
     auto grab = [&](int fixed) {
         if (!work) return fixed;
-        for (;;) {
-            int q = 0;
-            if (lane == 0) q = atomicAdd(work, 1);
-            q = __shfl_sync(FULL, q, 0);
-            if (q < nslow) return order.cur_list[q];
-            const int f = q - nslow;
-            if (f >= total || !order.cur_flag || !order.cur_flag[f]) return f;
-        }
+        int q = 0;
+        if (lane == 0) q = atomicAdd(work, 1);
+        return __shfl_sync(FULL, q, 0);
     };
     for (int f = grab(blockIdx.x * wpc + warp); f < total; f = grab(f + gridDim.x * wpc)) {
         const int p = cur.advance(prefix, count, f);
@@ -1098,17 +1085,11 @@ __global__ void __launch_bounds__(kWarps * 32)
         // X(t) + V: the X(t) cell of each column is the tile value + 1; Y itself in
         // the discretisation entry point
         const float zadd = sx_only ? 0.0f : 1.0f;
-        int singles = 0;
         const int ties = s.sx_kind == 1
                              ? pick_column<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic,
                                                    pis, swarm, t, zadd, newp)
                              : second_target<NW, VT>(s, tile, dead, em, nwr, n, lane, pic, pis, swarm, t, zadd,
-                                                     newp, singles);
-        if (order.nxt_flag && lane == 0) {  // the order of the next iteration
-            const bool slow = singles >= kSlowSingles;
-            order.nxt_flag[f] = slow ? 1 : 0;
-            if (slow) order.nxt_list[atomicAdd(order.nxt_cnt, 1)] = f;
-        }
+                                                     newp);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const int j = lane + 32 * w;
@@ -1128,7 +1109,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 }
 
 template <int NW, typename VT>
-cudaError_t launch_upd(const VsxLaunch& L, int parity, cudaStream_t st) {
+cudaError_t launch_upd(const VsxLaunch& L, cudaStream_t st) {
     int wpc = L.warps > 0 ? L.warps : kWarps;  // warps (particles) per CTA
     if (wpc > kWarps) wpc = kWarps;
     while (wpc > 1 && kBarBytes + wpc * warp_bytes<VT>(L.n_max) > kSmemLimit) --wpc;
@@ -1147,33 +1128,21 @@ cudaError_t launch_upd(const VsxLaunch& L, int parity, cudaStream_t st) {
         e = cudaMemsetAsync(L.d_work, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
     }
-    SlowOrder order{};
-    if (L.d_work && L.order_buf) {  // parity selects which buffer is read and which written
-        const int c = parity & 1, x = c ^ 1;
-        order.cur_list = L.order_buf->list[c];
-        order.cur_cnt = L.order_buf->cnt[c];
-        order.cur_flag = L.order_buf->flag[c];
-        order.nxt_list = L.order_buf->list[x];
-        order.nxt_cnt = L.order_buf->cnt[x];
-        order.nxt_flag = L.order_buf->flag[x];
-        e = cudaMemsetAsync(order.nxt_cnt, 0, sizeof(int32_t), st);
-        if (e != cudaSuccess) return e;
-    }
-    k_update<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work, order);
+    k_update<NW, VT><<<grid, wpc * 32, smem, st>>>(L.d_views, L.d_prefix, L.count, L.n_max, L.d_work);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t launch_upd_t(const VsxLaunch& L, int parity, cudaStream_t st) {
+cudaError_t launch_upd_t(const VsxLaunch& L, cudaStream_t st) {
     switch ((L.n_max + 31) / 32) {
-        case 1: return launch_upd<1, VT>(L, parity, st);
-        case 2: return launch_upd<2, VT>(L, parity, st);
-        case 3: return launch_upd<3, VT>(L, parity, st);
-        case 4: return launch_upd<4, VT>(L, parity, st);
-        case 5: return launch_upd<5, VT>(L, parity, st);
+        case 1: return launch_upd<1, VT>(L, st);
+        case 2: return launch_upd<2, VT>(L, st);
+        case 3: return launch_upd<3, VT>(L, st);
+        case 4: return launch_upd<4, VT>(L, st);
+        case 5: return launch_upd<5, VT>(L, st);
         case 6:
         case 7:
-        case 8: return launch_upd<8, VT>(L, parity, st);
+        case 8: return launch_upd<8, VT>(L, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1201,10 +1170,10 @@ cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_velocity_sx(const VsxLaunch& L, int parity, cudaStream_t st) {
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st) {
     if (L.total <= 0) return cudaSuccess;
     if (L.n_max > velocity_sx_max_n(L.v_bf16)) return cudaErrorInvalidValue;
-    return L.v_bf16 ? launch_upd_t<__nv_bfloat16>(L, parity, st) : launch_upd_t<float>(L, parity, st);
+    return L.v_bf16 ? launch_upd_t<__nv_bfloat16>(L, st) : launch_upd_t<float>(L, st);
 }
 
 }  // namespace qap

@@ -75,24 +75,6 @@ int ls_max_n(LsKind kind);
 // The update of every particle of `count` populations (flat index over particles):
 // velocity (Eq. 4 + S_v) and position (Eq. 5, S_x) in one kernel, one warp per
 // particle, V read and written once.
-// The order in which the update kernel hands out particles: those that took many
-// single greedy steps in the previous iteration first. Two buffers alternate by
-// iteration parity (the one read, the one written for the next iteration); list and
-// flag of a buffer always agree (flag[f] = 1 exactly for the f in list[0, cnt)), so every
-// particle is processed exactly once whatever the order.
-struct SlowOrderBuf {
-    int32_t* list[2];  // total entries each (flat particle indices)
-    int32_t* cnt[2];
-    uint8_t* flag[2];  // total entries each
-};
-struct SlowOrder {     // one launch's view: read cur, write nxt (all null: plain order)
-    const int32_t* cur_list;
-    const int32_t* cur_cnt;
-    const uint8_t* cur_flag;
-    int32_t* nxt_list;
-    int32_t* nxt_cnt;
-    uint8_t* nxt_flag;
-};
 struct VsxLaunch {
     const StateView* d_views;
     const int32_t* d_prefix;  // count + 1 particle offsets
@@ -103,10 +85,8 @@ struct VsxLaunch {
     int warps;                // warps per CTA (0 = automatic)
     int32_t* d_work;          // the kernel's particle counter (zeroed before each
                               // launch), or null for a fixed grid-stride order
-    const SlowOrderBuf* order_buf;  // host copy of the order buffers' device pointers, or null
 };
-// parity: the iteration's parity as counted by the caller (selects the order buffers)
-cudaError_t launch_velocity_sx(const VsxLaunch& L, int parity, cudaStream_t st);
+cudaError_t launch_velocity_sx(const VsxLaunch& L, cudaStream_t st);
 int velocity_sx_max_n(int v_bf16);
 
 cudaError_t launch_init(const StateView& s, int v_bf16, cudaStream_t st);

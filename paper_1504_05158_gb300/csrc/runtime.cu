@@ -100,16 +100,8 @@ cudaError_t reinit_state(pso_state* s, cudaStream_t st) {
     return e;
 }
 
-void drop_graphs(pso_state* s) {
-    for (int p = 0; p < 2; ++p) {
-        if (s->g1[p]) cudaGraphExecDestroy(s->g1[p]);
-        if (s->g16[p]) cudaGraphExecDestroy(s->g16[p]);
-        s->g1[p] = s->g16[p] = nullptr;
-    }
-}
-
 cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
-                             const TimedParts& T, uint64_t* launched, float* ms_out) {
+                             const TimedParts& T, float* ms_out) {
     if (iterations <= 0) return cudaSuccess;
     constexpr int E = 4;  // update (velocity + S_x), search, bests
     std::vector<cudaEvent_t> ev((size_t)iterations * E, nullptr);
@@ -120,7 +112,7 @@ cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, s
         cudaEvent_t* q = &ev[(size_t)i * E];
         if (flush_buf && flush_bytes) e = cudaMemsetAsync(flush_buf, i & 0xFF, flush_bytes, st);
         if (e == cudaSuccess) e = cudaEventRecord(q[0], st);
-        if (e == cudaSuccess) e = launch_velocity_sx(*T.vsx, (int)((*launched)++ & 1), st);
+        if (e == cudaSuccess) e = launch_velocity_sx(*T.vsx, st);
         if (e == cudaSuccess) e = cudaEventRecord(q[1], st);
         for (int g = 0; g < T.nls && e == cudaSuccess; ++g) e = launch_ls(T.ls[g], st);
         if (e == cudaSuccess) e = cudaEventRecord(q[2], st);
@@ -151,8 +143,8 @@ cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, s
 
 namespace {
 
-cudaError_t enqueue_iteration(pso_state* s, int parity) {
-    cudaError_t e = launch_velocity_sx(s->vsx, parity, s->stream);
+cudaError_t enqueue_iteration(pso_state* s) {
+    cudaError_t e = launch_velocity_sx(s->vsx, s->stream);
     if (e != cudaSuccess) return e;
     e = launch_ls(s->ls_iter, s->stream);
     if (e != cudaSuccess) return e;
@@ -161,12 +153,12 @@ cudaError_t enqueue_iteration(pso_state* s, int parity) {
     return e;
 }
 
-cudaError_t capture(pso_state* s, int iters, int parity, cudaGraphExec_t* out) {
+cudaError_t capture(pso_state* s, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < iters; ++i) {
-        e = enqueue_iteration(s, (parity + i) & 1);
+        e = enqueue_iteration(s);
         if (e != cudaSuccess) break;
     }
     cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
@@ -362,7 +354,6 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     const size_t ostb = take((size_t)sl * 8), osto = take(8 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
     const size_t owork = take(3 * 4);  // search (iteration, set-up), position
-    const size_t oord = take(2 * ((size_t)P * 4 + (size_t)P + 16));  // the update kernel's particle order
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -400,12 +391,6 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->d_prefix = (int32_t*)(base + opre);
     s->d_ls = (LsArgs*)(base + ols);
     s->d_work = (int32_t*)(base + owork);
-    for (int b = 0; b < 2; ++b) {
-        char* ob = base + oord + (size_t)b * ((size_t)P * 4 + (size_t)P + 16);
-        s->order.cnt[b] = (int32_t*)ob;
-        s->order.list[b] = (int32_t*)(ob + 16);
-        s->order.flag[b] = (uint8_t*)(ob + 16 + (size_t)P * 4);
-    }
     sv.seed = seed;
     sv.c1 = params->c1;
     sv.c2 = params->c2;
@@ -428,8 +413,7 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->h_ls[1] = ls_args_for(s, true, s->d_work + 1);
     s->h_prefix[0] = 0;
     s->h_prefix[1] = P;
-    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0, s->d_work + 2,
-                       &s->order};
+    s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0, s->d_work + 2};
     s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     e = cudaMemsetAsync(base, 0, off, s->stream);
@@ -459,8 +443,7 @@ int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
     size_t t = align_up(P * vstride * esz, a) + 3 * align_up(P * ps, a) + 2 * align_up(P * 8, a) +
                2 * align_up(P * 4, a) + 2 * align_up(m * ps, a) + 2 * align_up(m * 8, a) + 4 * a +
                align_up(kResHead + ps, a) + align_up(sl * 8, a) + align_up(8 * 8, a) +
-               align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a +
-               align_up(2 * (P * 4 + P + 16), a);
+               align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a;
     *bytes = t;
     return QAP_OK;
 }
@@ -483,17 +466,17 @@ int pso_step(pso_state_t s, int32_t iterations) {
     if (!s || iterations < 0) return QAP_ERR_INVALID_ARG;
     if (iterations == 0) return QAP_OK;
     cudaError_t e = cudaSuccess;
+    if (!s->g1) e = capture(s, 1, &s->g1);
+    if (e == cudaSuccess && iterations >= 16 && !s->g16) e = capture(s, 16, &s->g16);
+    if (e != cudaSuccess) return status_of(e);
     int left = iterations;
+    while (left >= 16 && e == cudaSuccess) {
+        e = cudaGraphLaunch(s->g16, s->stream);
+        left -= 16;
+    }
     while (left > 0 && e == cudaSuccess) {
-        const int p = (int)(s->launched & 1);
-        const bool big = left >= 16;
-        cudaGraphExec_t* g = big ? &s->g16[p] : &s->g1[p];
-        if (!*g) e = capture(s, big ? 16 : 1, p, g);
-        if (e == cudaSuccess) e = cudaGraphLaunch(*g, s->stream);
-        if (e == cudaSuccess) {
-            s->launched += big ? 16 : 1;
-            left -= big ? 16 : 1;
-        }
+        e = cudaGraphLaunch(s->g1, s->stream);
+        --left;
     }
     return status_of(e);
 }
@@ -502,7 +485,7 @@ int pso_step_timed(pso_state_t s, int32_t iterations, void* flush_buf, size_t fl
                    float* ms_out) {
     if (!s || iterations < 0 || !ms_out) return QAP_ERR_INVALID_ARG;
     const TimedParts T{&s->vsx, &s->ls_iter, 1, s->d_view, 1, s->sv.m};
-    return status_of(timed_iterations(s->stream, iterations, flush_buf, flush_bytes, T, &s->launched, ms_out));
+    return status_of(timed_iterations(s->stream, iterations, flush_buf, flush_bytes, T, ms_out));
 }
 
 int pso_best(pso_state_t s, int64_t* cost, int32_t* perm, int32_t* iter_found) {
@@ -588,7 +571,8 @@ int pso_cost_histogram(pso_state_t s, int32_t swarm, int64_t lo, int64_t hi, int
 void pso_destroy(pso_state_t s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    drop_graphs(s);
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->g16) cudaGraphExecDestroy(s->g16);
     if (s->trace.d) cudaFree(s->trace.d);
     cudaFree(s->dbase);
     if (s->h_res) cudaFreeHost(s->h_res);
@@ -967,8 +951,8 @@ int pso_discretize(const float* Y, const int32_t* Z, int32_t n, int32_t count, c
     if (e == cudaSuccess) e = cudaMemset(base + oC, 0, CNT_N * 8);
     if (e == cudaSuccess)
         e = launch_velocity_sx(VsxLaunch{(const StateView*)(base + oView), (const int32_t*)(base + oPre), 1, n,
-                                         count, 0, 0, nullptr, nullptr},
-                               0, 0);
+                                         count, 0, 0, nullptr},
+                               0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     unsigned long long cnt[CNT_N] = {};
     if (e == cudaSuccess) e = cudaMemcpy(cnt, base + oC, sizeof(cnt), cudaMemcpyDeviceToHost);

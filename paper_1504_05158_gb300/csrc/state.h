@@ -41,9 +41,7 @@ struct pso_state {
     int32_t h_prefix[2];
     qap::VsxLaunch vsx;
     qap::LsLaunch ls_iter, ls_init;
-    cudaGraphExec_t g1[2], g16[2];  // by the parity of the first iteration they run
-    uint64_t launched;        // iterations queued so far (their parity orders the particles)
-    qap::SlowOrderBuf order;  // device buffers of the update kernel's particle order
+    cudaGraphExec_t g1, g16;
     bool borrowed;            // a member of a batch (the batch runs its iterations)
     qap::TraceBuf trace;      // per-iteration statistics (off unless pso_trace_start)
     unsigned char* h_res;     // pinned: best cost, iteration and permutation (pso_best)
@@ -64,9 +62,7 @@ struct TimedParts {
 // [0] the update (velocity and S_x, one kernel), [1] goal function + local search,
 // [2] bests + migration, [3] whole iterations, [4] 0 (kept for the layout).
 cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, size_t flush_bytes,
-                             const TimedParts& T, uint64_t* launched, float* ms_out);
-// releases the captured graphs of a state (they are captured again when needed)
-void drop_graphs(pso_state* s);
+                             const TimedParts& T, float* ms_out);
 int status_of(cudaError_t e);
 LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work);
 cudaError_t reinit_state(pso_state* s, cudaStream_t st);

@@ -250,7 +250,9 @@ int pso_trace_start(pso_state_t s, int32_t capacity, int64_t lo, int64_t hi, int
     s->trace.lo = lo;
     s->trace.hi = hi;
     // the captured iterations change: capture them again at the next pso_step
-    drop_graphs(s);
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->g16) cudaGraphExecDestroy(s->g16);
+    s->g1 = s->g16 = nullptr;
     return QAP_OK;
 }
 
@@ -286,7 +288,9 @@ int pso_trace_stop(pso_state_t s) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (s->trace.d) cudaFree(s->trace.d);
     s->trace = TraceBuf{};
-    drop_graphs(s);
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->g16) cudaGraphExecDestroy(s->g16);
+    s->g1 = s->g16 = nullptr;
     return status_of(e);
 }
 

@@ -216,7 +216,19 @@ struct StateView {
     int32_t sx_only;
     const int32_t* sx_swarm;
     const int32_t* sx_pis;
+    // The order in which the iteration's search hands out particles (null: index
+    // order). The update kernel appends particle p to list ord_list[b P ..] of bucket
+    // b = ord_bucket(d), d the number of positions where S_x moved p away from X(t);
+    // the search takes the buckets from the highest down (a particle moved far from its
+    // last local optimum tends to need many moves); k_bests zeroes the counts.
+    int32_t* ord_cnt;   // kOrdBuckets counts
+    int32_t* ord_list;  // kOrdBuckets x P particle indices
 };
+
+constexpr int kOrdBuckets = 8;
+__host__ __device__ inline int ord_bucket(int d) {
+    return d <= 2 ? 0 : d <= 4 ? 1 : d <= 6 ? 2 : d <= 8 ? 3 : d <= 12 ? 4 : d <= 16 ? 5 : d <= 24 ? 6 : 7;
+}
 
 // counters[CNT_ERR] counts internal consistency failures (a kernel that detects one
 // skips the access instead of faulting; the host reports it).

@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(kThreads) k_bests(const StateView* __restrict_
     int* ord = sb_idx + m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int t = *s.t;
+    // the search of this iteration has used the update kernel's buckets: empty them
+    if (s.ord_cnt && threadIdx.x < kOrdBuckets) s.ord_cnt[threadIdx.x] = 0;
 
     // each swarm's best current particle
     for (int k = warp; k < m; k += nwarps) {

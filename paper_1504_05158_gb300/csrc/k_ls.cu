@@ -221,12 +221,34 @@ __device__ __forceinline__ void store_cost_only(const LsArgs& a, int p, long lon
     __syncwarp();
 }
 
-// the next particle of warp-per-particle kernels: from the population's counter,
-// else a fixed stride
-__device__ __forceinline__ int next_particle(const LsArgs& a, int& p, int stride, int lane) {
+// Whether the update kernel's buckets hold every particle of the population exactly
+// once (their counts add up to the population), so that the hand-out can follow them.
+__device__ __forceinline__ bool ord_ready(const LsArgs& a) {
+    if (!a.ord_cnt || !a.ord_list) return false;
+    int tot = 0;
+#pragma unroll
+    for (int b = 0; b < kOrdBuckets; ++b) tot += a.ord_cnt[b];
+    return tot == a.count;
+}
+// The q-th particle handed out: the buckets from the highest down (particles that S_x
+// moved farthest first), else index order.
+__device__ __forceinline__ int ord_pick(const LsArgs& a, bool ready, int q) {
+    if (!ready || q >= a.count) return q;
+    int rem = q;
+    for (int b = kOrdBuckets - 1; b >= 0; --b) {
+        const int c = a.ord_cnt[b];
+        if (rem < c) return a.ord_list[(size_t)b * a.count + rem];
+        rem -= c;
+    }
+    return q;
+}
+
+// the next particle of warp-per-particle kernels: from the population's counter (in
+// the update kernel's order when it is ready), else a fixed stride
+__device__ __forceinline__ int next_particle(const LsArgs& a, bool ready, int& p, int stride, int lane) {
     if (a.work) {
         int q = 0;
-        if (lane == 0) q = atomicAdd(a.work, 1);
+        if (lane == 0) q = ord_pick(a, ready, atomicAdd(a.work, 1));
         return __shfl_sync(FULL, q, 0);
     }
     const int cur = p;
@@ -278,8 +300,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls(const LsArgs* __res
     const int gs = n + 1;
 
     int pnext = cb * wpc + warp;
+    const bool ready = ord_ready(a);
     for (;;) {
-        const int pcur = next_particle(a, pnext, cpi * wpc, lane);
+        const int pcur = next_particle(a, ready, pnext, cpi * wpc, lane);
         if (pcur >= a.count) break;
         for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)pcur * a.ps_in + m];
         __syncwarp();
@@ -411,8 +434,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * 32) k_ls_direct(const LsArgs
     int32_t* pi = reinterpret_cast<int32_t*>(wb0 + (size_t)warp * direct_warp_bytes(n));
     const long long npairs = (long long)n * (n - 1) / 2;
     int pnext = cb * wpc + warp;
+    const bool ready = ord_ready(a);
     for (;;) {
-        const int p = next_particle(a, pnext, cpi * wpc, lane);
+        const int p = next_particle(a, ready, pnext, cpi * wpc, lane);
         if (p >= a.count) break;
         for (int m = lane; m < n; m += 32) pi[m] = a.in[(size_t)p * a.ps_in + m];
         __syncwarp();
@@ -915,11 +939,12 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
     uint32_t phase = 0;
     int next = cb * TEAMS + team;
     const int stride = cpi * TEAMS;
+    const bool ready = ord_ready(a);
 
     for (;;) {
         int p;
         if (a.work) {
-            if (tt == 0) xch[60] = atomicAdd(a.work, 1);
+            if (tt == 0) xch[60] = ord_pick(a, ready, atomicAdd(a.work, 1));
             team_sync<WPP>(team);
             p = xch[60];
             team_sync<WPP>(team);
@@ -1433,11 +1458,12 @@ __global__ void __launch_bounds__(256, 2) k_ls_gen(const LsArgs* __restrict__ ar
     const int nph = 256 / slotw, ph = tid / slotw, col = tid % slotw;
     uint32_t phase = 0;
     int next = cb;
+    const bool ready = ord_ready(a);
 
     for (;;) {
         int p;
         if (a.work) {
-            if (tid == 0) xch[60] = atomicAdd(a.work, 1);
+            if (tid == 0) xch[60] = ord_pick(a, ready, atomicAdd(a.work, 1));
             team_sync<8>(0);
             p = xch[60];
             team_sync<8>(0);

@@ -1096,6 +1096,16 @@ __global__ void __launch_bounds__(kWarps * 32)
             if (j < n) s.Xsx[(size_t)p * s.ps + j] = (uint8_t)newp[w];
         }
         if (lane == 0 && ties) atomicAdd(s.counters + CNT_TIES, (unsigned long long)ties);
+        if (s.ord_cnt) {  // the search's hand-out order: bucket of the distance moved
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) d += __popc(__ballot_sync(FULL, lane + 32 * w < n && newp[w] != pic[w]));
+            if (lane == 0) {
+                const int b = ord_bucket(d);
+                const int slot = atomicAdd(s.ord_cnt + b, 1);
+                if (slot < s.P) s.ord_list[(size_t)b * s.P + slot] = p;  // else the search keeps index order
+            }
+        }
         if (!sx_only) {
             __syncwarp();  // S_x has read the tile
             if (!new_v) velocity();

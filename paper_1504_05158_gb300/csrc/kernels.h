@@ -41,6 +41,8 @@ struct LsArgs {
     int32_t sym;       // F and D symmetric with zero diagonal
     int32_t exact32;   // n max_f max_d < 2^27 and max_d <= 65535: the int32 SIMT search is exact
     int32_t force;     // a LsKind chosen by the caller, or -1 (ls_kind decides)
+    const int32_t* ord_cnt;   // the hand-out order of the iteration's particles (the
+    const int32_t* ord_list;  // update kernel's buckets, StateView::ord_*), or null
 };
 
 // Which local-search kernel serves a population, and the launch shape.

@@ -87,6 +87,10 @@ LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work) {
     a.exact32 = s->inst->exact32 && s->inst->narrow_ok;
     a.force = -1;
     a.work = work;
+    if (!init) {  // the iteration's search follows the update kernel's order
+        a.ord_cnt = s->sv.ord_cnt;
+        a.ord_list = s->sv.ord_list;
+    }
     return a;
 }
 
@@ -354,6 +358,7 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     const size_t ostb = take((size_t)sl * 8), osto = take(8 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
     const size_t owork = take(3 * 4);  // search (iteration, set-up), position
+    const size_t oordc = take(kOrdBuckets * 4), oordl = take((size_t)kOrdBuckets * P * 4);  // search order
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -391,6 +396,8 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->d_prefix = (int32_t*)(base + opre);
     s->d_ls = (LsArgs*)(base + ols);
     s->d_work = (int32_t*)(base + owork);
+    sv.ord_cnt = (int32_t*)(base + oordc);
+    sv.ord_list = (int32_t*)(base + oordl);
     sv.seed = seed;
     sv.c1 = params->c1;
     sv.c2 = params->c2;
@@ -443,7 +450,8 @@ int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
     size_t t = align_up(P * vstride * esz, a) + 3 * align_up(P * ps, a) + 2 * align_up(P * 8, a) +
                2 * align_up(P * 4, a) + 2 * align_up(m * ps, a) + 2 * align_up(m * 8, a) + 4 * a +
                align_up(kResHead + ps, a) + align_up(sl * 8, a) + align_up(8 * 8, a) +
-               align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a;
+               align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a +
+               align_up(kOrdBuckets * 4, a) + align_up(kOrdBuckets * P * 4, a);
     *bytes = t;
     return QAP_OK;
 }

@@ -506,6 +506,13 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
     // plain cell instead, every X(t) cell was below the largest plain value, so the
     // test is skipped (single steps give the same result in every case).
     bool try_round = true;
+    // Nonzero: the key of the maximum the next step is known to have. After a step at
+    // value g that leaves a plain cell at g (its column's cache is exact), every other
+    // remaining cell is at most g, so the next step has the same maximum: it skips the
+    // round test (no X(t) cell can exceed a plain value g), the rebuilds (a stale bound
+    // lies below g) and the warp maximum. Not carried across the end of the exclusion
+    // phase, where ignored X(t) cells return.
+    uint32_t cont_key = 0u;
     for (int step = 0; step < n;) {
         const bool use_ex = step < depth;
         if (!use_ex) {
@@ -520,7 +527,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
 #pragma unroll
         for (int w = 0; w < NW; ++w) zin[w] = alive[w] && zal[w] && !(use_ex && ex[w]);
 
-        if (!use_ex && try_round) {
+        if (!use_ex && try_round && !cont_key) {
             // ---- a round of X(t) cells above every remaining plain value ----
             {
                 bool need[NW];
@@ -624,7 +631,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         // 2 the plain maximum alone
         uint32_t key[NW];
         int cnt[NW], mode[NW];
-        {
+        if (!cont_key) {
             bool need[NW];
 #pragma unroll
             for (int w = 0; w < NW; ++w) need[w] = alive[w] && vc[w] == 0 && !(zin[w] && zv[w] > vm[w]);
@@ -658,7 +665,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         uint32_t lm = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) lm = max(lm, key[w]);
-        const uint32_t gm = __reduce_max_sync(FULL, lm);
+        const uint32_t gm = cont_key ? cont_key : __reduce_max_sync(FULL, lm);
         // the elements of M per column (c = lane + 32 w ascending); while every count
         // is below 8, three ballots of their low bits give each slot's total and every
         // lane's inclusive prefix without a shuffle scan
@@ -804,6 +811,13 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
                     if (--vc[w] == 0) vm[w] = v2[w];  // the maximum's rows are gone: the bound below it
                 }
             }
+        }
+        {
+            bool plain_at_g = false;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) plain_at_g = plain_at_g || (alive[w] && vc[w] > 0 && fkey(vm[w]) == gm);
+            const bool same_ex = (step + 1 < depth) == use_ex;
+            cont_key = (same_ex && __any_sync(FULL, plain_at_g)) ? gm : 0u;
         }
         ++step;
     }

@@ -223,6 +223,7 @@ struct StateView {
     // last local optimum tends to need many moves); k_bests zeroes the counts.
     int32_t* ord_cnt;   // kOrdBuckets counts
     int32_t* ord_list;  // kOrdBuckets x P particle indices
+    int32_t ord_resets; // counts k_bests zeroes from ord_cnt on (those of the parts too)
 };
 
 constexpr int kOrdBuckets = 8;

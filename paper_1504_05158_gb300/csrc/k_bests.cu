@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kThreads) k_bests(const StateView* __restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int t = *s.t;
     // the search of this iteration has used the update kernel's buckets: empty them
-    if (s.ord_cnt && threadIdx.x < kOrdBuckets) s.ord_cnt[threadIdx.x] = 0;
+    if (s.ord_cnt)
+        for (int i = threadIdx.x; i < s.ord_resets; i += blockDim.x) s.ord_cnt[i] = 0;
 
     // each swarm's best current particle
     for (int k = warp; k < m; k += nwarps) {

@@ -148,9 +148,22 @@ cudaError_t timed_iterations(cudaStream_t st, int iterations, void* flush_buf, s
 namespace {
 
 cudaError_t enqueue_iteration(pso_state* s) {
-    cudaError_t e = launch_velocity_sx(s->vsx, s->stream);
-    if (e != cudaSuccess) return e;
-    e = launch_ls(s->ls_iter, s->stream);
+    cudaError_t e = cudaSuccess;
+    if (s->nsplit > 1) {
+        // fork: part h's update and search on its own stream; join before the bests
+        e = cudaEventRecord(s->ev_fork, s->stream);
+        for (int h = 1; h < s->nsplit && e == cudaSuccess; ++h) e = cudaStreamWaitEvent(s->aux[h - 1], s->ev_fork, 0);
+        for (int h = 0; h < s->nsplit && e == cudaSuccess; ++h)
+            e = launch_velocity_sx(s->pvsx[h], h ? s->aux[h - 1] : s->stream);
+        for (int h = 0; h < s->nsplit && e == cudaSuccess; ++h) e = launch_ls(s->pls[h], h ? s->aux[h - 1] : s->stream);
+        for (int h = 1; h < s->nsplit && e == cudaSuccess; ++h) {
+            e = cudaEventRecord(s->ev_join[h - 1], s->aux[h - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join[h - 1], 0);
+        }
+    } else {
+        e = launch_velocity_sx(s->vsx, s->stream);
+        if (e == cudaSuccess) e = launch_ls(s->ls_iter, s->stream);
+    }
     if (e != cudaSuccess) return e;
     e = launch_bests(s->d_view, 1, s->sv.m, 0, s->stream);
     if (e == cudaSuccess && s->trace.d) e = launch_trace(s->sv, s->trace, s->stream);
@@ -358,7 +371,11 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     const size_t ostb = take((size_t)sl * 8), osto = take(8 * 8);
     const size_t oview = take(sizeof(StateView)), opre = take(2 * 4), ols = take(2 * sizeof(LsArgs));
     const size_t owork = take(3 * 4);  // search (iteration, set-up), position
-    const size_t oordc = take(kOrdBuckets * 4), oordl = take((size_t)kOrdBuckets * P * 4);  // search order
+    // the search order: counts of the whole population, then of each part; one list area
+    // (a part's lists lie in the range of its own particles)
+    const size_t oordc = take(kOrdBuckets * 4 * (1 + kMaxSplit)), oordl = take((size_t)kOrdBuckets * P * 4);
+    const size_t opview = take(kMaxSplit * sizeof(StateView)), opls = take(kMaxSplit * sizeof(LsArgs));
+    const size_t opprefix = take(2 * kMaxSplit * 4), opwork = take(2 * kMaxSplit * 4);
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
@@ -398,6 +415,10 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->d_work = (int32_t*)(base + owork);
     sv.ord_cnt = (int32_t*)(base + oordc);
     sv.ord_list = (int32_t*)(base + oordl);
+    s->d_pview = (StateView*)(base + opview);
+    s->d_pls = (LsArgs*)(base + opls);
+    s->d_pprefix = (int32_t*)(base + opprefix);
+    s->d_pwork = (int32_t*)(base + opwork);
     sv.seed = seed;
     sv.c1 = params->c1;
     sv.c2 = params->c2;
@@ -423,10 +444,78 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->vsx = VsxLaunch{s->d_view, s->d_prefix, 1, n, P, params->v_storage == PSO_V_BF16, 0, s->d_work + 2};
     s->ls_iter = LsLaunch{s->d_ls, s->d_work, 1, n, (int)ls_kind(s->h_ls[0]), 0, P};
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
+    // parts of whole swarms for the captured iterations: views and searches over their
+    // particles (pointers advanced to the part's first particle and swarm; the draws
+    // keyed by the swarm's index in the run, as for a part of a split run)
+    s->nsplit = m >= 2 ? kMaxSplit : 1;
+    sv.ord_resets = kOrdBuckets * (1 + s->nsplit);
+    StateView h_pview[kMaxSplit] = {};
+    LsArgs h_pls[kMaxSplit] = {};
+    int32_t h_pprefix[2 * kMaxSplit] = {};
+    if (s->nsplit > 1) {
+        const size_t vbytes = (size_t)sv.vstride * esz;
+        for (int h = 0, fs = 0; h < s->nsplit; ++h) {
+            const int cs = m / s->nsplit + (h < m % s->nsplit ? 1 : 0);  // swarms of part h
+            const size_t fp = (size_t)fs * ss;
+            const int cp = cs * ss;
+            StateView pv = sv;
+            pv.m = cs;
+            pv.P = cp;
+            pv.swarm_base = sv.swarm_base + fs;
+            pv.V = (char*)sv.V + fp * vbytes;
+            pv.X += fp * sv.ps;
+            pv.Xsx += fp * sv.ps;
+            pv.PL += fp * sv.ps;
+            pv.costL += fp;
+            pv.cost += fp;
+            pv.moves += fp;
+            pv.rounds += fp;
+            pv.PG += (size_t)fs * sv.ps;
+            pv.PG2 += (size_t)fs * sv.ps;
+            pv.costG += fs;
+            pv.costG2 += fs;
+            pv.ord_cnt = sv.ord_cnt + kOrdBuckets * (1 + h);
+            pv.ord_list = sv.ord_list + (size_t)kOrdBuckets * fp;
+            pv.ord_resets = 0;
+            h_pview[h] = pv;
+            LsArgs a = ls_args_for(s, false, s->d_pwork + 2 * h + 1);
+            a.count = cp;
+            a.in = pv.Xsx;
+            a.out = pv.X;
+            a.cost = pv.cost;
+            a.moves = pv.moves;
+            a.rounds = pv.rounds;
+            a.PL = pv.PL;
+            a.costL = pv.costL;
+            a.ord_cnt = pv.ord_cnt;
+            a.ord_list = pv.ord_list;
+            h_pls[h] = a;
+            h_pprefix[2 * h + 1] = cp;
+            s->pvsx[h] = VsxLaunch{s->d_pview + h, s->d_pprefix + 2 * h, 1, n, cp,
+                                   params->v_storage == PSO_V_BF16, 0, s->d_pwork + 2 * h};
+            s->pls[h] = LsLaunch{s->d_pls + h, s->d_pwork + 2 * h + 1, 1, n, (int)ls_kind(a), 0, cp};
+            fs += cs;
+        }
+        for (int h = 0; h + 1 < s->nsplit && e == cudaSuccess; ++h) {
+            e = cudaStreamCreateWithFlags(&s->aux[h], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join[h], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            pso_destroy(s);
+            return status_of(e);
+        }
+    }
     e = cudaMemsetAsync(base, 0, off, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_view, &s->sv, sizeof(StateView), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_prefix, s->h_prefix, sizeof(s->h_prefix), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(s->h_ls), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && s->nsplit > 1)
+        e = cudaMemcpyAsync(s->d_pview, h_pview, sizeof(h_pview), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && s->nsplit > 1)
+        e = cudaMemcpyAsync(s->d_pls, h_pls, sizeof(h_pls), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && s->nsplit > 1)
+        e = cudaMemcpyAsync(s->d_pprefix, h_pprefix, sizeof(h_pprefix), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = reinit_state(s, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -451,7 +540,9 @@ int pso_footprint(int32_t n, const pso_params_t* p, size_t* bytes) {
                2 * align_up(P * 4, a) + 2 * align_up(m * ps, a) + 2 * align_up(m * 8, a) + 4 * a +
                align_up(kResHead + ps, a) + align_up(sl * 8, a) + align_up(8 * 8, a) +
                align_up(sizeof(StateView), a) + a + align_up(2 * sizeof(LsArgs), a) + a +
-               align_up(kOrdBuckets * 4, a) + align_up(kOrdBuckets * P * 4, a);
+               align_up(kOrdBuckets * 4 * (1 + kMaxSplit), a) + align_up(kOrdBuckets * P * 4, a) +
+               align_up(kMaxSplit * sizeof(StateView), a) + align_up(kMaxSplit * sizeof(LsArgs), a) +
+               2 * align_up(2 * kMaxSplit * 4, a);
     *bytes = t;
     return QAP_OK;
 }
@@ -581,6 +672,14 @@ void pso_destroy(pso_state_t s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->g1) cudaGraphExecDestroy(s->g1);
     if (s->g16) cudaGraphExecDestroy(s->g16);
+    for (int h = 0; h + 1 < kMaxSplit; ++h) {
+        if (s->aux[h]) {
+            cudaStreamSynchronize(s->aux[h]);
+            cudaStreamDestroy(s->aux[h]);
+        }
+        if (s->ev_join[h]) cudaEventDestroy(s->ev_join[h]);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->trace.d) cudaFree(s->trace.d);
     cudaFree(s->dbase);
     if (s->h_res) cudaFreeHost(s->h_res);

@@ -22,6 +22,8 @@ struct qap_instance {
 
 // One population. Its kernels read it through one-entry device tables (the same
 // kernels serve a batch of many populations with longer tables).
+constexpr int kMaxSplit = 2;
+
 struct pso_state {
     qap_instance* inst;
     pso_params_t prm;
@@ -41,6 +43,19 @@ struct pso_state {
     int32_t h_prefix[2];
     qap::VsxLaunch vsx;
     qap::LsLaunch ls_iter, ls_init;
+    // The captured iterations run the update and the search in `nsplit` parts of whole
+    // swarms, each part on its own branch of the graph (part 0 on `stream`, part h on
+    // aux[h - 1]), so the kernels of one part fill the SMs that the end of another
+    // part's kernel leaves idle; bests and migration join them. nsplit 1: no parts.
+    int nsplit;
+    qap::StateView* d_pview;       // nsplit part views
+    qap::LsArgs* d_pls;            // nsplit part searches
+    int32_t* d_pprefix;            // nsplit x {0, part particles}
+    int32_t* d_pwork;              // nsplit x {update, search} counters
+    qap::VsxLaunch pvsx[kMaxSplit];
+    qap::LsLaunch pls[kMaxSplit];
+    cudaStream_t aux[kMaxSplit - 1];
+    cudaEvent_t ev_fork, ev_join[kMaxSplit - 1];
     cudaGraphExec_t g1, g16;
     bool borrowed;            // a member of a batch (the batch runs its iterations)
     qap::TraceBuf trace;      // per-iteration statistics (off unless pso_trace_start)

@@ -577,8 +577,8 @@ __host__ __device__ inline TeamLayout<WPP, ET> team_layout(int n, bool allow_sme
     L.tDp = o;
     o += round128((size_t)n * L.dps * ES);
     L.tPi = o;                       // p as bytes, KP entries (zero padded)
-    L.tFd = L.tPi + align16(L.KP);   // int2 per row
-    L.tEv = L.tFd + align16((size_t)n * 8);
+    L.tFd = L.tPi + align16(L.KP);   // the compacted rows of a move: int4 per row, then a count per warp
+    L.tEv = L.tFd + align16((size_t)round_up(n, 32) * 16 + 32);
     L.tX = L.tEv + align16((size_t)n * 4);
     L.tBar = L.tX + kXchBytes;
     L.team_bytes = round128(L.tBar + 8);
@@ -681,9 +681,13 @@ __device__ __forceinline__ long long team_sum64(long long v, long long* xch, int
 // threads form `nph` phases of `slotw` threads: thread (ph, e) evaluates pair slot e
 // of virtual rows ph, ph + nph, ... (row t joined with row n-2-t) and, after a move,
 // updates column e of H in rows ph, ph + nph, ...
+// When the instance bounds the swap values enough for 32-bit keys (key_l = kl > 0), the
+// table holds every word scaled by 2^(2 kl), and the words above the diagonal also hold
+// their pair's index (k << kl | m): the two words of a pair then add up to its search
+// key S 2^(2 kl) + (k << kl | m), with nothing else to form per pair.
 template <int WPP, typename ET>
 __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* sF, int32_t* H, ET* Dp,
-                                             uint8_t* pi8, int2* fdv, int32_t* ev, int* xch, long long cost,
+                                             uint8_t* pi8, int4* seg, int32_t* ev, int* xch, long long cost,
                                              int gs, int dps, int tt, int team) {
     constexpr int TT = 32 * WPP;
     const int n = a.n;
@@ -693,6 +697,8 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
     const bool on = ph < nph && e < n;
     const long long npairs = (long long)n * (n - 1) / 2;
     const int nv = n / 2;
+    const int nseg = (n + 31) >> 5;  // warps whose threads hold rows in A
+    int* segc = reinterpret_cast<int*>(seg + 32 * nseg);
     int moves = 0, rounds = 0;
     if (a.max_moves >= 0) {
         const int kl = a.key_l, sh = 2 * kl;
@@ -719,11 +725,11 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
             if (kl > 0) {
                 int b0 = INT_MAX, b1 = INT_MAX, b2 = INT_MAX, b3 = INT_MAX;
                 if (on) {
+                    // the pair's two table words add up to its key
                     auto pv = [&](int t) -> int {
                         int k, m;
                         const bool ok = pair_of(t, k, m);
-                        const int sv = H[k * gs + m] + H[m * gs + k];
-                        const int v = (int)(((unsigned)sv << sh) | (unsigned)((k << kl) | m));
+                        const int v = H[k * gs + m] + H[m * gs + k];
                         return ok ? v : INT_MAX;
                     };
                     int t = ph;
@@ -783,7 +789,12 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
             // holds H + F o Dp)
             const int Frs = sF[r * n + s], Drs = Dp[r * dps + s];
             const int frd = Frs * Drs;
-            const int hrs = H[r * gs + s] - frd, hsr = H[s * gs + r] - frd;
+            // table words back to values (the pair index sits below bit sh); values to words
+            auto val = [&](int wv) { return wv >> sh; };
+            auto word = [&](int v, int k, int m) {
+                return (int)((unsigned)v << sh) + (k < m && kl > 0 ? ((k << kl) | m) : 0);
+            };
+            const int hrs = val(H[r * gs + s]) - frd, hsr = val(H[s * gs + r]) - frd;
             int fx = 0, ex = 0, drx = 0, dsx = 0, hxr = 0, hxs = 0, hrx = 0, hsx = 0, Fxr = 0, Fxs = 0;
             const int x = tt;
             if (x < n) {
@@ -793,51 +804,68 @@ __device__ __forceinline__ void descend_team(const LsArgs& a, int p, const ET* s
                 drx = Dp[r * dps + x];
                 dsx = Dp[s * dps + x];
                 ex = dsx - drx;
-                hxr = H[x * gs + r] - Fxr * drx;
-                hxs = H[x * gs + s] - Fxs * dsx;
-                hrx = H[r * gs + x] - Fxr * drx;
-                hsx = H[s * gs + x] - Fxs * dsx;
-                fdv[x] = make_int2((x == r || x == s) ? 0 : fx, fx * ex);
+                hxr = val(H[x * gs + r]) - Fxr * drx;
+                hxs = val(H[x * gs + s]) - Fxs * dsx;
+                hrx = val(H[r * gs + x]) - Fxr * drx;
+                hsx = val(H[s * gs + x]) - Fxs * dsx;
                 ev[x] = ex;
             }
+            {
+                // the rows B changes (fd != 0, outside {r, s}), compacted per warp: the row's
+                // word offset and the rank-1 term in table words (fd scaled by 2^sh, the
+                // pair index bits stay)
+                const bool act = x < n && x != r && x != s && fx != 0;
+                const unsigned bal = __ballot_sync(FULL, act);
+                const int wseg = tt >> 5;
+                if (act) {
+                    const int fxs = (int)((unsigned)fx << sh);
+                    seg[32 * wseg + __popc(bal & ((1u << lane) - 1u))] = make_int4(x * gs, fxs, fxs * ex, 0);
+                }
+                if (lane == 0 && wseg < nseg) segc[wseg] = __popc(bal);
+            }
             team_sync<WPP>(team);
-            // B: rows and columns outside {r, s} (F o Dp does not change there); rows
-            // with fd = 0 do not change
+            // B: rows and columns outside {r, s} (F o Dp does not change there), over the
+            // compacted rows whose fd is not zero (the others do not change)
             if (on && e != r && e != s) {
                 const int ec = ev[e];
-                int k = ph;
-                for (; k + 3 * nph < n; k += 4 * nph) {
-                    const int2 q0 = fdv[k], q1 = fdv[k + nph], q2 = fdv[k + 2 * nph], q3 = fdv[k + 3 * nph];
-                    int32_t* h0 = H + k * gs + e;
-                    int32_t* h1 = h0 + nph * gs;
-                    int32_t* h2 = h1 + nph * gs;
-                    int32_t* h3 = h2 + nph * gs;
-                    const int g0 = q0.x ? *h0 : 0, g1 = q1.x ? *h1 : 0, g2 = q2.x ? *h2 : 0, g3 = q3.x ? *h3 : 0;
-                    if (q0.x) *h0 = g0 + q0.x * ec - q0.y;
-                    if (q1.x) *h1 = g1 + q1.x * ec - q1.y;
-                    if (q2.x) *h2 = g2 + q2.x * ec - q2.y;
-                    if (q3.x) *h3 = g3 + q3.x * ec - q3.y;
-                }
-                for (; k < n; k += nph) {
-                    const int2 q = fdv[k];
-                    if (q.x) H[k * gs + e] += q.x * ec - q.y;
+                int32_t* col = H + e;
+                for (int w = 0; w < nseg; ++w) {
+                    const int c = segc[w];
+                    const int4* q = seg + 32 * w;
+                    int i = ph;
+                    for (; i + 3 * nph < c; i += 4 * nph) {
+                        const int4 q0 = q[i], q1 = q[i + nph], q2 = q[i + 2 * nph], q3 = q[i + 3 * nph];
+                        int32_t* h0 = col + q0.x;
+                        int32_t* h1 = col + q1.x;
+                        int32_t* h2 = col + q2.x;
+                        int32_t* h3 = col + q3.x;
+                        const int g0 = *h0, g1 = *h1, g2 = *h2, g3 = *h3;
+                        *h0 = g0 + q0.y * ec - q0.z;
+                        *h1 = g1 + q1.y * ec - q1.z;
+                        *h2 = g2 + q2.y * ec - q2.z;
+                        *h3 = g3 + q3.y * ec - q3.z;
+                    }
+                    for (; i < c; i += nph) {
+                        const int4 q0 = q[i];
+                        col[q0.x] += q0.y * ec - q0.z;
+                    }
                 }
             }
             // C: rows and columns r and s (e[r] = Drs, e[s] = -Drs, fd[r] = -Frs,
             // fd[s] = Frs), each with F o Dp of the swapped Dp (Dp[x][r] <- Dp[x][s])
             if (x < n && x != r && x != s) {
-                H[x * gs + r] = hxs - fx * (Drs + ex) + Fxr * dsx;
-                H[x * gs + s] = hxr + fx * (Drs - ex) + Fxs * drx;
-                H[r * gs + x] = hrx - hrs - Frs * (ex + Drs) + Fxr * dsx;
-                H[s * gs + x] = hsx - hsr + Frs * (ex - Drs) + Fxs * drx;
+                H[x * gs + r] = word(hxs - fx * (Drs + ex) + Fxr * dsx, x, r);
+                H[x * gs + s] = word(hxr + fx * (Drs - ex) + Fxs * drx, x, s);
+                H[r * gs + x] = word(hrx - hrs - Frs * (ex + Drs) + Fxr * dsx, r, x);
+                H[s * gs + x] = word(hsx - hsr + Frs * (ex - Drs) + Fxs * drx, s, x);
                 Dp[x * dps + r] = (ET)dsx;
                 Dp[x * dps + s] = (ET)drx;
                 Dp[r * dps + x] = (ET)dsx;
                 Dp[s * dps + x] = (ET)drx;
             }
             if (tt == 0) {
-                H[r * gs + s] = -hrs - frd;  // -hrs - 2 Frs Drs, plus F[r][s] Dp[r][s] (unchanged)
-                H[s * gs + r] = -hsr - frd;
+                H[r * gs + s] = word(-hrs - frd, r, s);  // -hrs - 2 Frs Drs, plus F[r][s] Dp[r][s] (unchanged)
+                H[s * gs + r] = word(-hsr - frd, s, r);
                 const uint8_t t8 = pi8[r];
                 pi8[r] = pi8[s];
                 pi8[s] = t8;
@@ -894,7 +922,7 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
     int32_t* H = reinterpret_cast<int32_t*>(U);
     ET* Dp = reinterpret_cast<ET*>(tb + L.tDp);
     uint8_t* pi8 = tb + L.tPi;
-    int2* fdv = reinterpret_cast<int2*>(tb + L.tFd);
+    int4* seg = reinterpret_cast<int4*>(tb + L.tFd);
     int32_t* ev = reinterpret_cast<int32_t*>(tb + L.tEv);
     int* xch = reinterpret_cast<int*>(tb + L.tX);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tb + L.tBar);
@@ -929,6 +957,7 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
     tc::fence_after_sync();
     const uint32_t tcol = *tslot + (uint32_t)(team * team_groups<ET>() * L.NP);
     const uint32_t idesc = tc::idesc_f16_f32(128, L.NP);
+    const int tkl = a.key_l, tsh = 2 * tkl;  // the table's word format (descend_team)
     const uint32_t sbo = (uint32_t)(KP / 8) * 128;
     const int rowbase = 32 * ((team * WPP) & 3);  // the lane quarter of the team's first warp
     const uint32_t a_base = smem_u32(sA) - (uint32_t)(rowbase / 8) * sbo;
@@ -1061,9 +1090,13 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
                     if (k < n) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q)
-                            if (c + q < n)
-                                H[k * gs + c + q] = __float2int_rn(__uint_as_float(v[q])) - d +
-                                                    (int)sF[(c + q) * n + k] * (int)Dp[(c + q) * dps + k];
+                            if (c + q < n) {
+                                const int hv = __float2int_rn(__uint_as_float(v[q])) - d +
+                                               (int)sF[(c + q) * n + k] * (int)Dp[(c + q) * dps + k];
+                                // a table word (scaled, with the pair index above the diagonal)
+                                H[k * gs + c + q] = (int)((unsigned)hv << tsh) +
+                                                    (k < c + q && tkl > 0 ? ((k << tkl) | (c + q)) : 0);
+                            }
                     }
                 }
             }
@@ -1074,7 +1107,7 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         for (int m = tt; m < n; m += TT) part += ev[m];
         const long long cost = team_sum64<WPP>(part, reinterpret_cast<long long*>(xch) + 16, team, lane, tt >> 5);
         team_sync<WPP>(team);
-        descend_team<WPP, ET>(a, p, sF, H, Dp, pi8, fdv, ev, xch, cost, gs, dps, tt, team);
+        descend_team<WPP, ET>(a, p, sF, H, Dp, pi8, seg, ev, xch, cost, gs, dps, tt, team);
         team_sync<WPP>(team);
     }
     tc::fence_before_sync();

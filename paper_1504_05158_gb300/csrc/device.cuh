@@ -158,6 +158,11 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 // waits until the issuing thread's bulk stores have finished reading shared memory
+// A hint that brings `bytes` (a multiple of 16, from a 16-byte aligned address) of
+// global memory into L2 ahead of a later bulk load.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // waits until the issuing thread's bulk stores are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }

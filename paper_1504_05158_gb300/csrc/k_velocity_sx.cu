@@ -115,49 +115,49 @@ struct ColMax {
 };
 
 // The maximum of column c over the remaining rows other than pz; em (the column's
-// mask, words 32 apart) receives the rows holding it.
+// mask, words 32 apart) receives the rows holding it. Two passes over the column: the
+// maximum first, then the rows equal to it and the largest value below it. Both read
+// eight rows at a time with independent loads and keep four partial results, so the
+// scan holds few registers (it sets the update kernel's register budget).
 template <typename VT>
-__device__ __noinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz, uint32_t* em) {
+__device__ __forceinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz, uint32_t* em) {
     const float kNegInf = __int_as_float(0xff800000);
-    ColMax r{kNegInf, 0, kNegInf};
-    for (int base = 0, wi = 0; base < n; base += 32, ++wi) {
+    const int nw = (n + 31) >> 5;
+    auto okbits = [&](int wi) {
         uint32_t ok = ~dead[wi];
         if ((pz >> 5) == wi) ok &= ~(1u << (pz & 31));
-        const int lim = n - base;
+        const int lim = n - 32 * wi;
         if (lim < 32) ok &= (1u << lim) - 1u;
-        float v[32];
-#pragma unroll
-        for (int b = 0; b < 32; ++b)
-            v[b] = ((ok >> b) & 1u) ? VStore<VT>::to_f(tile[(base + b) * n + c]) : kNegInf;
-        float mx = v[0];
-#pragma unroll
-        for (int b = 1; b < 32; ++b) mx = fmaxf(mx, v[b]);
-        uint32_t eq = 0u;
-        float sm = kNegInf;  // the largest value of the word below its maximum
-#pragma unroll
+        return ok;
+    };
+    float m4[4] = {kNegInf, kNegInf, kNegInf, kNegInf};
+    for (int wi = 0; wi < nw; ++wi) {
+        const uint32_t ok = okbits(wi);
+        const VT* col = tile + (size_t)(32 * wi) * n + c;
+#pragma unroll 8
         for (int b = 0; b < 32; ++b) {
-            eq |= (((ok >> b) & 1u) && v[b] == mx) ? (1u << b) : 0u;
-            sm = fmaxf(sm, v[b] < mx ? v[b] : kNegInf);
+            const float v = ((ok >> b) & 1u) ? VStore<VT>::to_f(col[b * n]) : kNegInf;
+            m4[b & 3] = fmaxf(m4[b & 3], v);
         }
-        uint32_t keep = 0u;
-        if (eq) {
-            if (r.cnt == 0 || mx > r.v) {
-                for (int k = 0; k < wi; ++k) em[32 * k] = 0u;  // a larger maximum: earlier rows leave
-                r.v2 = fmaxf(fmaxf(r.cnt ? r.v : kNegInf, r.v2), sm);
-                r.v = mx;
-                r.cnt = __popc(eq);
-                keep = eq;
-            } else if (mx == r.v) {
-                r.cnt += __popc(eq);
-                r.v2 = fmaxf(r.v2, sm);
-                keep = eq;
-            } else {
-                r.v2 = fmaxf(r.v2, mx);
-            }
-        }
-        em[32 * wi] = keep;
     }
-    return r;
+    const float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
+    float s4[4] = {kNegInf, kNegInf, kNegInf, kNegInf};
+    int cnt = 0;
+    for (int wi = 0; wi < nw; ++wi) {
+        const uint32_t ok = okbits(wi);
+        const VT* col = tile + (size_t)(32 * wi) * n + c;
+        uint32_t eq = 0u;
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+            const float v = ((ok >> b) & 1u) ? VStore<VT>::to_f(col[b * n]) : kNegInf;
+            eq |= (((ok >> b) & 1u) && v == mx) ? (1u << b) : 0u;
+            s4[b & 3] = fmaxf(s4[b & 3], v < mx ? v : kNegInf);
+        }
+        em[32 * wi] = eq;
+        cnt += __popc(eq);
+    }
+    const float v2 = fmaxf(fmaxf(s4[0], s4[1]), fmaxf(s4[2], s4[3]));
+    return ColMax{cnt ? mx : kNegInf, cnt, v2};
 }
 
 // The float of an order key (fkey's inverse; +0 for the key of +-0).
@@ -1018,8 +1018,22 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
 // particles are handed out one at a time from a counter (their cost varies with the
 // ties of the greedy), else in a fixed grid-stride order. The discretisation entry
 // point (sx_only) runs S_x alone on Y.
+// Blocks per SM the update kernel is compiled for (n <= 64): fp32 tiles (16 KB at
+// n = 64) let shared memory hold three 4-warp blocks, and the registers are capped so
+// that three fit; bf16 tiles (8 KB) leave room for more than four, so the registers
+// are capped at 128 per thread to let four blocks (16 warps) run. Larger n keep the
+// registers they need.
 template <int NW, typename VT>
-__global__ void __launch_bounds__(kWarps * 32)
+struct UpdBlocks {
+    static constexpr int kMin = NW <= 2 ? 3 : 1;
+};
+template <int NW>
+struct UpdBlocks<NW, __nv_bfloat16> {
+    static constexpr int kMin = NW <= 2 ? 4 : 1;
+};
+
+template <int NW, typename VT>
+__global__ void __launch_bounds__(kWarps * 32, UpdBlocks<NW, VT>::kMin)
     k_update(const StateView* __restrict__ views, const int32_t* __restrict__ prefix, int count, int n_max,
              int32_t* __restrict__ work) {
     const int wpc = blockDim.x >> 5;
@@ -1043,7 +1057,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (lane == 0) q = atomicAdd(work, 1);
         return __shfl_sync(FULL, q, 0);
     };
-    for (int f = grab(blockIdx.x * wpc + warp); f < total; f = grab(f + gridDim.x * wpc)) {
+    int fnext = total;
+    for (int f = grab(blockIdx.x * wpc + warp); f < total; f = fnext) {
         const int p = cur.advance(prefix, count, f);
         const StateView s = views[cur.inst];
         const int n = s.n;
@@ -1110,6 +1125,16 @@ __global__ void __launch_bounds__(kWarps * 32)
             if (j < n) s.Xsx[(size_t)p * s.ps + j] = (uint8_t)newp[w];
         }
         if (lane == 0 && ties) atomicAdd(s.counters + CNT_TIES, (unsigned long long)ties);
+        // the warp's next particle, taken once S_x is done: its tile is fetched into L2
+        // while the velocity and the store of this one run
+        fnext = grab(f + gridDim.x * wpc);
+        if (lane == 0 && fnext < total) {
+            TableCursor nc = cur;
+            const int pn = nc.advance(prefix, count, fnext);
+            const StateView* sv = views + nc.inst;
+            bulk_prefetch_l2(reinterpret_cast<const VT*>(sv->V) + (size_t)pn * sv->vstride,
+                             (uint32_t)tile_bytes<VT>(sv->n));
+        }
         if (s.ord_cnt) {  // the search's hand-out order: bucket of the distance moved
             int d = 0;
 #pragma unroll

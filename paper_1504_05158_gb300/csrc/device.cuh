@@ -158,6 +158,17 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 // waits until the issuing thread's bulk stores have finished reading shared memory
+// (a.x b.x, a.y b.y), each product rounded to nearest like __fmul_rn, in one
+// paired fp32 instruction
+__device__ __forceinline__ float2 fmul2_rn(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x)),
+          "l"(((unsigned long long)__float_as_uint(b.y) << 32) | __float_as_uint(b.x)));
+    return make_float2(__uint_as_float((uint32_t)d), __uint_as_float((uint32_t)(d >> 32)));
+}
+
 // A hint that brings `bytes` (a multiple of 16, from a 16-byte aligned address) of
 // global memory into L2 ahead of a later bulk load.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {

@@ -952,8 +952,15 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
             }
         }
         float inv0 = 1.0f, inv1 = 1.0f;
+        // With Norm, the clamp of the plain cells is usually idle (|c1 v| <= v_max for
+        // every v of the two columns): the first pass forms the column sums of |c1 v| and
+        // the largest |c1 v|; only when that exceeds v_max are the sums formed again from
+        // the clamped values. Either way the sums and the stored values are those of
+        // clamp(c1 v).
+        bool unclamped = false;
         if (norm) {
             float px[4] = {0.f, 0.f, 0.f, 0.f}, py[4] = {0.f, 0.f, 0.f, 0.f};
+            float mxy = 0.0f;
             int i = 0;
             for (; i + 3 < n; i += 4) {
                 float x[4], y[4];
@@ -961,15 +968,42 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
                 for (int u = 0; u < 4; ++u) Pair<VT>::get(tile + (i + u) * n + j0, x[u], y[u]);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    px[u] += fabsf(wgen(x[u]));
-                    py[u] += fabsf(wgen(y[u]));
+                    const float2 g = fmul2_rn(make_float2(x[u], y[u]), make_float2(c1, c1));
+                    const float gx = fabsf(g.x), gy = fabsf(g.y);
+                    px[u] += gx;
+                    py[u] += gy;
+                    mxy = fmaxf(mxy, fmaxf(gx, gy));
                 }
             }
             for (; i < n; ++i) {
                 float x0, y0;
                 Pair<VT>::get(tile + i * n + j0, x0, y0);
-                px[0] += fabsf(wgen(x0));
-                py[0] += fabsf(wgen(y0));
+                const float gx = fabsf(__fmul_rn(c1, x0)), gy = fabsf(__fmul_rn(c1, y0));
+                px[0] += gx;
+                py[0] += gy;
+                mxy = fmaxf(mxy, fmaxf(gx, gy));
+            }
+            unclamped = mxy <= vmax;
+            if (!unclamped) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) px[u] = py[u] = 0.0f;
+                i = 0;
+                for (; i + 3 < n; i += 4) {
+                    float x[4], y[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) Pair<VT>::get(tile + (i + u) * n + j0, x[u], y[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        px[u] += fabsf(wgen(x[u]));
+                        py[u] += fabsf(wgen(y[u]));
+                    }
+                }
+                for (; i < n; ++i) {
+                    float x0, y0;
+                    Pair<VT>::get(tile + i * n + j0, x0, y0);
+                    px[0] += fabsf(wgen(x0));
+                    py[0] += fabsf(wgen(y0));
+                }
             }
             float s0 = (px[0] + px[1]) + (px[2] + px[3]), s1 = (py[0] + py[1]) + (py[2] + py[3]);
 #pragma unroll
@@ -983,6 +1017,19 @@ __device__ __noinline__ void velocity_pairs(VT* tile, int n, int lane, const uin
             inv1 = s1 > 0.0f ? 1.0f / s1 : 1.0f;
         }
         int i = 0;
+        if (unclamped) {
+            for (; i + 3 < n; i += 4) {
+                float x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) Pair<VT>::get(tile + (i + u) * n + j0, x[u], y[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 g = fmul2_rn(fmul2_rn(make_float2(x[u], y[u]), make_float2(c1, c1)),
+                                              make_float2(inv0, inv1));
+                    Pair<VT>::put(tile + (i + u) * n + j0, g.x, g.y);
+                }
+            }
+        }
         for (; i + 3 < n; i += 4) {
             float x[4], y[4];
 #pragma unroll

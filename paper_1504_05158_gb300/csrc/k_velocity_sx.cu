@@ -116,9 +116,11 @@ struct ColMax {
 
 // The maximum of column c over the remaining rows other than pz; em (the column's
 // mask, words 32 apart) receives the rows holding it. Two passes over the column: the
-// maximum first, then the rows equal to it and the largest value below it. Both read
-// eight rows at a time with independent loads and keep four partial results, so the
-// scan holds few registers (it sets the update kernel's register budget).
+// maximum first, then the rows equal to it and the value below it. Each reads kScanU
+// rows at a time with independent loads into kScanU partial results: few registers
+// (the scan sets the update kernel's register budget) and little code (a small loop
+// body keeps the kernel's hot code in the instruction cache).
+constexpr int kScanU = 4;
 template <typename VT>
 __device__ __forceinline__ ColMax vscan(const VT* tile, const uint32_t* dead, int n, int c, int pz, uint32_t* em) {
     const float kNegInf = __int_as_float(0xff800000);
@@ -130,33 +132,47 @@ __device__ __forceinline__ ColMax vscan(const VT* tile, const uint32_t* dead, in
         if (lim < 32) ok &= (1u << lim) - 1u;
         return ok;
     };
-    float m4[4] = {kNegInf, kNegInf, kNegInf, kNegInf};
+    float mu[kScanU];
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) mu[u] = kNegInf;
     for (int wi = 0; wi < nw; ++wi) {
         const uint32_t ok = okbits(wi);
         const VT* col = tile + (size_t)(32 * wi) * n + c;
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
-            const float v = ((ok >> b) & 1u) ? VStore<VT>::to_f(col[b * n]) : kNegInf;
-            m4[b & 3] = fmaxf(m4[b & 3], v);
+#pragma unroll 1
+        for (int b = 0; b < 32; b += kScanU) {
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const float v = ((ok >> (b + u)) & 1u) ? VStore<VT>::to_f(col[(b + u) * n]) : kNegInf;
+                mu[u] = fmaxf(mu[u], v);
+            }
         }
     }
-    const float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
-    float s4[4] = {kNegInf, kNegInf, kNegInf, kNegInf};
+    float mx = mu[0];
+#pragma unroll
+    for (int u = 1; u < kScanU; ++u) mx = fmaxf(mx, mu[u]);
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) mu[u] = kNegInf;
     int cnt = 0;
     for (int wi = 0; wi < nw; ++wi) {
         const uint32_t ok = okbits(wi);
         const VT* col = tile + (size_t)(32 * wi) * n + c;
         uint32_t eq = 0u;
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
-            const float v = ((ok >> b) & 1u) ? VStore<VT>::to_f(col[b * n]) : kNegInf;
-            eq |= (((ok >> b) & 1u) && v == mx) ? (1u << b) : 0u;
-            s4[b & 3] = fmaxf(s4[b & 3], v < mx ? v : kNegInf);
+#pragma unroll 1
+        for (int b = 0; b < 32; b += kScanU) {
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const bool in = (ok >> (b + u)) & 1u;
+                const float v = in ? VStore<VT>::to_f(col[(b + u) * n]) : kNegInf;
+                eq |= (in && v == mx) ? (1u << (b + u)) : 0u;
+                mu[u] = fmaxf(mu[u], v < mx ? v : kNegInf);
+            }
         }
         em[32 * wi] = eq;
         cnt += __popc(eq);
     }
-    const float v2 = fmaxf(fmaxf(s4[0], s4[1]), fmaxf(s4[2], s4[3]));
+    float v2 = mu[0];
+#pragma unroll
+    for (int u = 1; u < kScanU; ++u) v2 = fmaxf(v2, mu[u]);
     return ColMax{cnt ? mx : kNegInf, cnt, v2};
 }
 

@@ -42,11 +42,14 @@ __host__ __device__ inline size_t mask_bytes(int n) {
     return w * w * 32 * sizeof(uint32_t);
 }
 __host__ __device__ inline size_t lists_bytes(int n) { return align16((size_t)(n > 64 ? n : 64)); }
+// The cells of a tie group (tie_group): up to 32 kGroupSlots per warp.
+constexpr int kGroupSlots = 4;
+constexpr size_t kGroupBytes = 32 * kGroupSlots * sizeof(uint32_t);
 template <typename VT>
 __host__ __device__ inline size_t warp_bytes(int n) {
     // + deleted-row bits (8 words) + the tail's row/column lists or PickColumn's order
-    // + the row masks
-    return tile_bytes<VT>(n) + 32 + lists_bytes(n) + mask_bytes(n);
+    // + the row masks + the tie group's cells
+    return tile_bytes<VT>(n) + 32 + lists_bytes(n) + mask_bytes(n) + kGroupBytes;
 }
 
 // --------------------------------------------------------------------- init
@@ -453,6 +456,163 @@ __device__ __forceinline__ int pick_column(const StateView& s, const VT* tile, u
     return ties;
 }
 
+// A run of steps of SecondTarget at one value g. When a step's set M (the remaining
+// cells equal to the largest remaining value g) has at least two and at most
+// 32 kGroupSlots elements, no other cell can reach g while M is not empty, so the next
+// steps draw from M alone until it is: M is listed once in its column-major order
+// (column, then row), one cell per lane and slot, and each step takes the k-th live
+// cell (k from the step's tie draw, as in a single step), deletes its row and column
+// and drops the cells that lie in either, with a few ballots per step. The run stops
+// when M is empty, at the end of the exclusion phase (the ignored X(t) cells return)
+// or, past that phase, when only X(t) cells are left in M (a round then takes them
+// together). Afterwards the caches of the remaining columns lose the deleted rows.
+// Inputs: the step's per-column counts cm, modes (0 the X(t) cell alone, 1 the plain
+// maximum and the X(t) cell, 2 the plain maximum alone), the three ballots of the
+// counts' bits and the per-slot totals tw. Returns -1 on an inconsistent list (which
+// cannot happen; counted as an error).
+template <int NW>
+__device__ __forceinline__ int tie_group(const StateView& s, uint32_t* dead, uint32_t* em, uint32_t* gl, int nwr,
+                                         int n, int lane, const int (&pic)[NW], bool (&alive)[NW], bool (&zal)[NW],
+                                         float (&vm)[NW], int (&vc)[NW], const float (&v2)[NW], int (&newp)[NW],
+                                         const int (&cm)[NW], const int (&mode)[NW], const unsigned (&b0)[NW],
+                                         const unsigned (&b1)[NW], const unsigned (&b2)[NW], const int (&tw)[NW],
+                                         int tot, int depth, bool use_ex, uint32_t pis, uint32_t swarm, uint32_t t,
+                                         int& step, int& ties, U4& tu, int& tblk) {
+    auto emw = [&](int w, int wi) -> uint32_t& { return em[(w * nwr + wi) * 32 + lane]; };
+    // list M: a column's cells go to positions [start, start + cm) in column order,
+    // each cell (X flag << 16) | (row << 8) | column
+    const unsigned le = (2u << lane) - 1u;
+    int base = 0;
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int incl = __popc(b0[w] & le) + 2 * __popc(b1[w] & le) + 4 * __popc(b2[w] & le);
+        if (cm[w] > 0) {
+            const int c = lane + 32 * w;
+            int o = base + incl - cm[w];
+            const int end = base + incl;
+            if (mode[w] == 0) {
+                gl[o++] = (1u << 16) | ((uint32_t)pic[w] << 8) | (uint32_t)c;
+            } else {
+#pragma unroll
+                for (int wi = 0; wi < NW; ++wi) {
+                    if (32 * wi >= n) continue;
+                    uint32_t m = emw(w, wi);
+                    if (mode[w] == 1 && (pic[w] >> 5) == wi) m |= 1u << (pic[w] & 31);
+                    while (m && o < end) {
+                        const int r = 32 * wi + __ffs(m) - 1;
+                        m &= m - 1u;
+                        gl[o++] = (r == pic[w] ? (1u << 16) : 0u) | ((uint32_t)r << 8) | (uint32_t)c;
+                    }
+                }
+            }
+            bad = bad || o != end;
+        }
+        base += tw[w];
+    }
+    if (__any_sync(FULL, bad)) {
+        if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+        return -1;
+    }
+    __syncwarp();
+    uint32_t cell[kGroupSlots];
+    unsigned bq[kGroupSlots];
+#pragma unroll
+    for (int q = 0; q < kGroupSlots; ++q) {
+        const int e = 32 * q + lane;
+        cell[q] = e < tot ? gl[e] : 0u;
+        bq[q] = __ballot_sync(FULL, e < tot);
+    }
+    uint32_t gone[NW];
+#pragma unroll
+    for (int wi = 0; wi < NW; ++wi) gone[wi] = 0u;
+    int left = tot;
+    for (;;) {
+        int k = 0;
+        if (left > 1) {
+            ++ties;
+            if (s.tie_rule == 0) {
+                if ((step >> 2) != tblk) {  // one block of draws serves four steps
+                    tu = draw(s.seed, pis, swarm, t, TAG_TIE, (uint32_t)(step >> 2));
+                    tblk = step >> 2;
+                }
+                k = (int)below(word_of(tu, step & 3), (uint32_t)left);
+            }
+        }
+        // the k-th live cell in list order (slot, then lane)
+        uint32_t mine = 0u, bsel = 0u;
+        bool found = false;
+#pragma unroll
+        for (int q = 0; q < kGroupSlots; ++q) {
+            const int cq = __popc(bq[q]);
+            if (!found && k < cq) {
+                mine = cell[q];
+                bsel = bq[q];
+                found = true;
+            } else if (!found) {
+                k -= cq;
+            }
+        }
+        const bool me = ((bsel >> lane) & 1u) && __popc(bsel & (le >> 1)) == k;
+        const int src = __ffs(__ballot_sync(FULL, me)) - 1;
+        if (src < 0) {  // cannot happen
+            if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
+            return -1;
+        }
+        const uint32_t pc = __shfl_sync(FULL, mine, src);
+        const int r = (int)((pc >> 8) & 0xFFu), c = (int)(pc & 0xFFu);
+        if (lane == (c & 31)) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (w == (c >> 5)) {
+                    newp[w] = r;
+                    alive[w] = false;
+                }
+        }
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi)
+            if (wi == (r >> 5)) gone[wi] |= 1u << (r & 31);
+        left = 0;
+        bool plain = false;
+#pragma unroll
+        for (int q = 0; q < kGroupSlots; ++q) {
+            const bool live = ((bq[q] >> lane) & 1u) && (int)((cell[q] >> 8) & 0xFFu) != r &&
+                              (int)(cell[q] & 0xFFu) != c;
+            bq[q] = __ballot_sync(FULL, live);
+            left += __popc(bq[q]);
+            plain = plain || (live && !(cell[q] >> 16));
+        }
+        ++step;
+        if (left == 0) break;
+        if (use_ex ? step >= depth : !__any_sync(FULL, plain)) break;
+    }
+    // the deleted rows leave the remaining columns' caches
+#pragma unroll
+    for (int wi = 0; wi < NW; ++wi)
+        if (lane == wi) dead[wi] |= gone[wi];
+    __syncwarp();
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (!alive[w]) continue;
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi)
+            if ((pic[w] >> 5) == wi && ((gone[wi] >> (pic[w] & 31)) & 1u)) zal[w] = false;
+        if (vc[w] == 0) continue;
+        int cnt = 0;
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi) {
+            if (32 * wi >= n) continue;
+            uint32_t& m = emw(w, wi);
+            const uint32_t mv = m;
+            if (mv & gone[wi]) m = mv & ~gone[wi];
+            cnt += __popc(mv & ~gone[wi]);
+        }
+        vc[w] = cnt;
+        if (cnt == 0) vm[w] = v2[w];  // the maximum's rows are gone: the bound below it
+    }
+    return 0;
+}
+
 // SecondTarget (Algorithm 1) on Y for one particle; returns the number of steps
 // whose set M had more than one element and leaves the location chosen for each
 // owned column (facility) in newp. The tile holds V with Y = X(t) + V (zadd = 1:
@@ -703,6 +863,15 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             tot += tw[w];
         }
         const bool wide = __any_sync(FULL, big);
+        if (!wide && tot >= 2 && tot <= 32 * kGroupSlots) {
+            // several cells at g: the steps at g run as one group
+            if (tie_group<NW>(s, dead, em, em + nwr * nwr * 32, nwr, n, lane, pic, alive, zal, vm, vc, v2, newp, cm,
+                              mode, b0, b1, b2, tw, tot, depth, use_ex, pis, swarm, t, step, ties, tu, tblk) < 0)
+                return ties;
+            try_round = true;
+            cont_key = 0u;
+            continue;
+        }
         int owner = -1, ow = 0, kk = 0;
         if (!wide) {
             int k = 0;

@@ -280,7 +280,9 @@ typedef struct {
 /* Copies the device state into caller-owned host buffers (synchronises). */
 int pso_export_state(pso_state_t st, pso_host_state_t* out);
 /* Overwrites the device state from host buffers (V values are rounded to the
- * storage format; X_sx and moves are ignored). Synchronises. */
+ * storage format; X_sx and moves are ignored). Every V value must be finite and
+ * every X, PL, PG and best row a permutation, else QAP_ERR_INVALID_ARG with the
+ * state untouched. Synchronises. */
 int pso_import_state(pso_state_t st, const pso_host_state_t* in);
 
 /* ---------------------------------------------------------------- batches */

@@ -41,7 +41,7 @@ __host__ __device__ inline size_t mask_bytes(int n) {
     const size_t w = (size_t)(n + 31) / 32;
     return w * w * 32 * sizeof(uint32_t);
 }
-__host__ __device__ inline size_t lists_bytes(int n) { return align16((size_t)(n > 64 ? n : 64)); }
+__host__ __device__ inline size_t lists_bytes(int n) { return align16((size_t)(n > 128 ? n : 128)); }
 // The cells of a tie group (tie_group): up to 32 kGroupSlots per warp.
 constexpr int kGroupSlots = 4;
 constexpr size_t kGroupBytes = 32 * kGroupSlots * sizeof(uint32_t);
@@ -220,6 +220,96 @@ __device__ __forceinline__ ColMax coscan(const VT* tile, const uint32_t* dead, i
     return ColMax{km ? unkey(km) : kNegInf, km ? cnt : 0, k2 ? unkey(k2) : kNegInf};
 }
 
+// The first cache build of SecondTarget, before any row is deleted: every owned
+// column at once, the columns' X(t) cells holding -inf in the tile (second_target
+// hides them), so no row needs a test. Pass 1 forms each column's maximum, pass 2 its
+// rows and the largest value below it; kScanU rows of every owned column per loop
+// step.
+template <int NW, typename VT>
+__device__ __forceinline__ void first_scan(const VT* tile, uint32_t* em, int nwr, int n, int lane,
+                                           const bool (&alive)[NW], float (&vm)[NW], int (&vc)[NW],
+                                           float (&v2)[NW]) {
+    const float kNegInf = __int_as_float(0xff800000);
+    float mu[NW][kScanU];
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) mu[w][u] = kNegInf;
+    const int nfull = n - n % kScanU;
+#pragma unroll 1
+    for (int i = 0; i < nfull; i += kScanU) {
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u)
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+                if (alive[w]) mu[w][u] = fmaxf(mu[w][u], VStore<VT>::to_f(tile[(i + u) * n + lane + 32 * w]));
+    }
+    for (int i = nfull; i < n; ++i)
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (alive[w]) mu[w][0] = fmaxf(mu[w][0], VStore<VT>::to_f(tile[i * n + lane + 32 * w]));
+    float mx[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        mx[w] = mu[w][0];
+#pragma unroll
+        for (int u = 1; u < kScanU; ++u) mx[w] = fmaxf(mx[w], mu[w][u]);
+#pragma unroll
+        for (int u = 0; u < kScanU; ++u) mu[w][u] = kNegInf;
+    }
+    int cnt[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt[w] = 0;
+    for (int wi = 0; 32 * wi < n; ++wi) {
+        uint32_t eq[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) eq[w] = 0u;
+        const int i1 = n < 32 * wi + 32 ? n : 32 * wi + 32;
+        const int i1f = i1 - (i1 - 32 * wi) % kScanU;
+#pragma unroll 1
+        for (int i = 32 * wi; i < i1f; i += kScanU) {
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const uint32_t bit = 1u << ((i + u) & 31);
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    if (!alive[w]) continue;
+                    const float v = VStore<VT>::to_f(tile[(i + u) * n + lane + 32 * w]);
+                    const bool at = v == mx[w];
+                    eq[w] |= at ? bit : 0u;
+                    mu[w][u] = fmaxf(mu[w][u], at ? kNegInf : v);
+                }
+            }
+        }
+        for (int i = i1f; i < i1; ++i) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                if (!alive[w]) continue;
+                const float v = VStore<VT>::to_f(tile[i * n + lane + 32 * w]);
+                const bool at = v == mx[w];
+                eq[w] |= at ? 1u << (i & 31) : 0u;
+                mu[w][0] = fmaxf(mu[w][0], at ? kNegInf : v);
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (!alive[w]) continue;
+            em[(w * nwr + wi) * 32 + lane] = eq[w];
+            cnt[w] += __popc(eq[w]);
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (!alive[w]) continue;
+        float b = mu[w][0];
+#pragma unroll
+        for (int u = 1; u < kScanU; ++u) b = fmaxf(b, mu[w][u]);
+        vm[w] = cnt[w] ? mx[w] : kNegInf;
+        vc[w] = cnt[w];
+        v2[w] = b;
+    }
+}
+
 // Rebuilds the caches of the owned columns that need it (need[w]): by the warp together
 // (coscan) when at most kCoopMax columns of a slot need it, else by each lane alone
 // (vscan, every lane scanning its own column at once).
@@ -267,11 +357,12 @@ constexpr int kTailCols = 11;  // kTailCols^2 <= 32 kTailSlots
 template <int NW, typename VT>
 __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const uint32_t* dead, uint8_t* lists,
                                        int n, int lane, const int (&pic)[NW], const bool (&alive)[NW],
-                                       uint32_t pis, uint32_t swarm, uint32_t t, float zadd, int step, int A,
-                                       U4& tu, int& tblk, int (&newp)[NW]) {
+                                       const float (&zv)[NW], uint32_t pis, uint32_t swarm, uint32_t t, int step,
+                                       int A, U4& tu, int& tblk, int (&newp)[NW]) {
     uint8_t* rows = lists;       // remaining rows, ascending
     uint8_t* cols = lists + 16;  // remaining columns, ascending
     uint8_t* xrow = lists + 32;  // their X(t) rows
+    float* xval = reinterpret_cast<float*>(lists + 64);  // and the Y values of their X(t) cells
     const unsigned below_me = (1u << lane) - 1u;
     int base = 0;
 #pragma unroll
@@ -290,6 +381,7 @@ __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const
             const int pos = base + __popc(am & below_me);
             cols[pos] = (uint8_t)(lane + 32 * w);
             xrow[pos] = (uint8_t)pic[w];
+            xval[pos] = zv[w];
         }
         base += __popc(am);
     }
@@ -304,8 +396,7 @@ __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const
         if (q < A * A) {
             const int ci = q / A, ri = q % A;
             const int r = rows[ri], c = cols[ci];
-            float y = VStore<VT>::to_f(tile[r * n + c]);
-            if (r == xrow[ci]) y += zadd;
+            const float y = r == xrow[ci] ? xval[ci] : VStore<VT>::to_f(tile[r * n + c]);
             key[sl] = fkey(y);
             rc[sl] = (ri << 8) | ci;
         }
@@ -517,11 +608,13 @@ __device__ __forceinline__ int tie_group(const StateView& s, uint32_t* dead, uin
     __syncwarp();
     uint32_t cell[kGroupSlots];
     unsigned bq[kGroupSlots];
+    const int nq = (tot + 31) >> 5;  // slots in use
 #pragma unroll
     for (int q = 0; q < kGroupSlots; ++q) {
         const int e = 32 * q + lane;
         cell[q] = e < tot ? gl[e] : 0u;
-        bq[q] = __ballot_sync(FULL, e < tot);
+        const int inq = tot - 32 * q;
+        bq[q] = inq >= 32 ? FULL : inq > 0 ? (1u << inq) - 1u : 0u;
     }
     uint32_t gone[NW];
 #pragma unroll
@@ -576,6 +669,7 @@ __device__ __forceinline__ int tie_group(const StateView& s, uint32_t* dead, uin
         bool plain = false;
 #pragma unroll
         for (int q = 0; q < kGroupSlots; ++q) {
+            if (q >= nq) continue;
             const bool live = ((bq[q] >> lane) & 1u) && (int)((cell[q] >> 8) & 0xFFu) != r &&
                               (int)(cell[q] & 0xFFu) != c;
             bq[q] = __ballot_sync(FULL, live);
@@ -625,7 +719,7 @@ __device__ __forceinline__ int tie_group(const StateView& s, uint32_t* dead, uin
 // one round; equal values among them only reorder those steps (each group of g
 // equal values is g - 1 steps with a choice). Other steps run one at a time.
 template <int NW, typename VT>
-__device__ __forceinline__ int second_target(const StateView& s, const VT* tile, uint32_t* dead, uint32_t* em,
+__device__ __forceinline__ int second_target(const StateView& s, VT* tile, uint32_t* dead, uint32_t* em,
                                              int nwr, int n, int lane, const int (&pic)[NW], uint32_t pis,
                                              uint32_t swarm, uint32_t t, float zadd, int (&newp)[NW]) {
     const int depth = s.depth;
@@ -648,6 +742,26 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         vc[w] = 0;
         newp[w] = 0;
     }
+    // The X(t) cells' values are kept in zv; while S_x runs, the tile holds -inf in
+    // their place, so that scans need no test for them; they are put back on return.
+    VT zraw[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (!alive[w]) continue;
+        VT& cell = tile[pic[w] * n + lane + 32 * w];
+        zraw[w] = cell;
+        cell = VStore<VT>::from_f(__int_as_float(0xff800000));
+    }
+    auto finish = [&](int ties_out) {
+        __syncwarp();
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (lane + 32 * w < n) tile[pic[w] * n + lane + 32 * w] = zraw[w];
+        __syncwarp();
+        return ties_out;
+    };
+    __syncwarp();
+    first_scan<NW, VT>(tile, em, nwr, n, lane, alive, vm, vc, v2);
     if (depth > 0) {
         if (s.sx_rule == 0) {
             // Algorithm 1 as printed: every element equal to 1 in Z = X(t) is ignored
@@ -695,7 +809,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             const int A = n - step;  // columns left
             if (A <= kTailCols) {
                 ties += sx_tail<NW, VT>(s, tile, dead, reinterpret_cast<uint8_t*>(dead + 8), n, lane, pic, alive,
-                                        pis, swarm, t, zadd, step, A, tu, tblk, newp);
+                                        zv, pis, swarm, t, step, A, tu, tblk, newp);
                 break;
             }
         }
@@ -867,7 +981,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
             // several cells at g: the steps at g run as one group
             if (tie_group<NW>(s, dead, em, em + nwr * nwr * 32, nwr, n, lane, pic, alive, zal, vm, vc, v2, newp, cm,
                               mode, b0, b1, b2, tw, tot, depth, use_ex, pis, swarm, t, step, ties, tu, tblk) < 0)
-                return ties;
+                return finish(ties);
             try_round = true;
             cont_key = 0u;
             continue;
@@ -979,7 +1093,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         if (!use_ex) try_round = (rx >> 16) != 0;
         if (owner < 0 || r < 0 || r >= n) {  // cannot happen; never index with it
             if (lane == 0) atomicAdd(s.counters + CNT_ERR, 1ull);
-            return ties;
+            return finish(ties);
         }
         __syncwarp();
         // the other columns lose row r
@@ -1006,7 +1120,7 @@ __device__ __forceinline__ int second_target(const StateView& s, const VT* tile,
         }
         ++step;
     }
-    return ties;
+    return finish(ties);
 }
 
 // The flat particle index f of a table of populations: the population and the

@@ -779,6 +779,7 @@ int pso_import_state(pso_state_t s, const pso_host_state_t* in) {
     for (int p = 0; p < P; ++p) {
         for (int k = 0; k < n * n; ++k) {
             const float f = in->V[(size_t)p * n * n + k];
+            if (!std::isfinite(f)) return QAP_ERR_INVALID_ARG;
             const size_t idx = (size_t)p * sv.vstride + k;
             if (bf) {
                 const uint16_t h = host_bf16(f);

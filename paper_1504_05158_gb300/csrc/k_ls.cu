@@ -990,6 +990,7 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
         // writes it as row j of Dp and of the B tile
         {
             const int parts = TT / L.NP;  // threads per row (NP <= TT)
+            const bool packed = a.Dpk != nullptr && !L.smem_d;
             if (tt < parts * L.NP) {
                 const int j = tt % L.NP, part = tt / L.NP;
                 const int pjv = j < n ? (int)pi8[j] : 0;
@@ -998,14 +999,26 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
                     if (j < n) {
                         const uint2 pm8 = *reinterpret_cast<const uint2*>(pi8 + c);
                         int v[8];
+                        if (packed) {  // fp16 bits and value in one word: no conversions
+                            uint32_t w[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int pmq = (int)(((q < 4 ? pm8.x : pm8.y) >> (8 * (q & 3))) & 0xFFu);
-                            v[q] = 0;
-                            if (c + q < n) v[q] = L.smem_d ? (int)sD[pmq * n + pjv] : __ldg(a.D + pmq * n + pjv);
+                            for (int q = 0; q < 8; ++q) {
+                                const int pmq = (int)(((q < 4 ? pm8.x : pm8.y) >> (8 * (q & 3))) & 0xFFu);
+                                w[q] = c + q < n ? __ldg(a.Dpk + pmq * n + pjv) : 0u;
+                                v[q] = (int)(w[q] & 0xFFFFu);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) h[q] = __byte_perm(w[2 * q], w[2 * q + 1], 0x7632);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const int pmq = (int)(((q < 4 ? pm8.x : pm8.y) >> (8 * (q & 3))) & 0xFFu);
+                                v[q] = 0;
+                                if (c + q < n) v[q] = L.smem_d ? (int)sD[pmq * n + pjv] : __ldg(a.D + pmq * n + pjv);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
                         }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) h[q] = pack_h2(v[2 * q], v[2 * q + 1]);
                         if (c + 8 <= n) {  // whole words of Dp (rows start on 4 bytes)
                             if (sizeof(ET) == 2) {
 #pragma unroll

@@ -388,13 +388,15 @@ __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const
     __syncwarp();
     uint32_t key[kTailSlots];
     int rc[kTailSlots];  // (row index << 8) | column index
+    // q / A as (q ceil(2^16 / A)) >> 16: exact for every q < A^2 with A <= kTailCols
+    const int inv_a = (65536 + A - 1) / A;
 #pragma unroll
     for (int sl = 0; sl < kTailSlots; ++sl) {
         const int q = lane + 32 * sl;
         key[sl] = 0u;  // no cell (every finite value has a nonzero key)
         rc[sl] = 0;
         if (q < A * A) {
-            const int ci = q / A, ri = q % A;
+            const int ci = (q * inv_a) >> 16, ri = q - ci * A;  // q / A, q % A
             const int r = rows[ri], c = cols[ci];
             const float y = r == xrow[ci] ? xval[ci] : VStore<VT>::to_f(tile[r * n + c]);
             key[sl] = fkey(y);

@@ -19,6 +19,8 @@ struct LsArgs {
     int32_t ps_in, ps_out;
     const int32_t* F;  // device n x n, symmetric with zero diagonal when max_moves >= 0
     const int32_t* D;  // device n x n
+    const uint32_t* Dpk;  // D as (fp16 bits << 16) | value when every entry is <= 2048 (the
+                          // tensor-core set-up gathers both from one word), else null
     const uint8_t* in;
     uint8_t* out;
     int64_t* cost;     // count

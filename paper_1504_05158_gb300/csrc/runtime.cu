@@ -27,6 +27,15 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr size_t kCntBytes = (CNT_N * 8 + 15) / 16 * 16;
 constexpr size_t kResHead = kCntBytes + 16;
 
+// fp16 bits of an integer 0 <= v <= 2048 (exact: at most 11 significant bits)
+uint16_t half_bits_small(int v) {
+    if (v <= 0) return 0;
+    int e = 0;
+    while ((v >> (e + 1)) != 0) ++e;  // floor(log2 v)
+    const uint32_t mant = e >= 10 ? ((uint32_t)v >> (e - 10)) & 0x3FFu : ((uint32_t)v << (10 - e)) & 0x3FFu;
+    return (uint16_t)(((uint32_t)(e + 15) << 10) | mant);
+}
+
 // host round-to-nearest-even float -> bfloat16 bits (finite inputs)
 uint16_t host_bf16(float f) {
     uint32_t b;
@@ -72,6 +81,7 @@ LsArgs ls_args_for(const pso_state* s, bool init, int32_t* work) {
     a.ps_in = a.ps_out = s->sv.ps;
     a.F = s->inst->dF;
     a.D = s->inst->dD;
+    a.Dpk = s->inst->dDpk;
     a.in = s->sv.Xsx;
     a.out = s->sv.X;
     a.cost = s->sv.cost;
@@ -246,9 +256,18 @@ int qap_create_instance(int32_t n, const int32_t* F, const int32_t* D, qap_insta
     if (e == cudaSuccess) e = cudaMalloc(&q->dD, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(q->dF, F, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(q->dD, D, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && (q->tc_exact & 1)) {
+        // D for the tensor-core set-up: each entry (<= 2048, exact in fp16) with its
+        // fp16 bits in the high half
+        std::vector<uint32_t> pk((size_t)n * n);
+        for (size_t i = 0; i < pk.size(); ++i) pk[i] = ((uint32_t)half_bits_small(D[i]) << 16) | (uint32_t)D[i];
+        e = cudaMalloc(&q->dDpk, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(q->dDpk, pk.data(), bytes, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(q->dF);
         cudaFree(q->dD);
+        cudaFree(q->dDpk);
         delete q;
         return status_of(e);
     }
@@ -260,6 +279,7 @@ void qap_destroy_instance(qap_instance_t inst) {
     if (!inst) return;
     cudaFree(inst->dF);
     cudaFree(inst->dD);
+    cudaFree(inst->dDpk);
     delete inst;
 }
 
@@ -835,6 +855,7 @@ static int run_ls_hook(qap_instance_t inst, int force, const int32_t* perms, int
     a.count = count;
     a.F = inst->dF;
     a.D = inst->dD;
+    a.Dpk = inst->dDpk;
     a.max_moves = max_moves;
     a.tc_exact = inst->tc_exact;
     a.key_l = inst->key_l;

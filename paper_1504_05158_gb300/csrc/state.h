@@ -11,6 +11,7 @@ struct qap_instance {
     int32_t n;
     int32_t* dF;
     int32_t* dD;
+    uint32_t* dDpk;  // tc_exact bit 0: D as (fp16 bits << 16) | value, else null
     int32_t sym_zd;
     int32_t max_f, max_d;
     int32_t exact32;    // n max_f max_d < 2^27

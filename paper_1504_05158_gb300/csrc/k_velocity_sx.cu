@@ -351,8 +351,8 @@ __device__ __forceinline__ void rebuild(const VT* tile, const uint32_t* dead, ui
 // run the greedy directly, one maximum and one ballot count per step. Cells are
 // numbered q = (column index) A + (row index) over the remaining columns and rows,
 // both ascending, which is the column-major order of M that the tie draw uses.
-constexpr int kTailSlots = 4;
-constexpr int kTailCols = 11;  // kTailCols^2 <= 32 kTailSlots
+constexpr int kTailSlots = 1;
+constexpr int kTailCols = 5;   // kTailCols^2 <= 32 kTailSlots
 
 template <int NW, typename VT>
 __device__ __forceinline__ int sx_tail(const StateView& s, const VT* tile, const uint32_t* dead, uint8_t* lists,

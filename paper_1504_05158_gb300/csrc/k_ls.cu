@@ -963,8 +963,6 @@ __global__ void __launch_bounds__(WPP == 2 ? 512 : 256, WPP == 1 ? 2 : 1)
     const uint32_t a_base = smem_u32(sA) - (uint32_t)(rowbase / 8) * sbo;
     const int wq = warp & 3;                      // this warp's lane quarter
     const bool reader = (warp % WPP) < 4;         // warps that read the team's rows back
-    const int slotw = round_up(n, 32) < TT ? round_up(n, 32) : TT;
-    const int nph = TT / slotw, ph = tt / slotw, col = tt % slotw;
     uint32_t phase = 0;
     int next = cb * TEAMS + team;
     const int stride = cpi * TEAMS;

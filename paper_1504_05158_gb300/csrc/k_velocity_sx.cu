@@ -1,6 +1,7 @@
-// Initialisation, the velocity update and the position update of every particle,
-// one warp per particle: the velocity kernel streams V through global memory, the
-// position kernel stages the particle's n x n tile in shared memory.
+// Initialisation, and the velocity and position updates of every particle in one
+// kernel (k_update), one warp per particle: the particle's n x n tile of V is staged in
+// shared memory with one bulk copy, S_x reads it, the velocity replaces it in place and
+// one bulk copy stores it back, so V is read and written once per iteration.
 //
 // Velocity (section 3.1, Eq. 4): W = c1 V(t) + c2 r2 (P^L - X(t)) + c3 r3 (P^G - X(t)),
 // V(t+1) = S_v(W); S_v Raw clamps to [-v_max, v_max], Norm then divides column j by
@@ -16,7 +17,9 @@
 // column then row; with random ties the k-th element is taken, k = floor(u |M| /
 // 2^32) with u from Philox. Lanes own columns and keep each column's maximum, its
 // multiplicity and the rows holding it (a bit mask) over the remaining rows, so a
-// step costs a warp reduction, a few ballots and one mask word per owned column.
+// step costs a warp reduction, a few ballots and one mask word per owned column;
+// steps that all draw from one set of equal maxima run as a tie group, and X(t)
+// cells above every remaining plain value are assigned together in a round.
 #include <climits>
 
 #include "kernels.h"

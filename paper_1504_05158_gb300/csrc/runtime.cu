@@ -466,8 +466,11 @@ static int init_state(qap_instance_t inst, const pso_params_t* params, uint64_t 
     s->ls_init = LsLaunch{s->d_ls + 1, s->d_work + 1, 1, n, (int)ls_kind(s->h_ls[1]), 0, P};
     // parts of whole swarms for the captured iterations: views and searches over their
     // particles (pointers advanced to the part's first particle and swarm; the draws
-    // keyed by the swarm's index in the run, as for a part of a split run)
-    s->nsplit = m >= 2 ? kMaxSplit : 1;
+    // keyed by the swarm's index in the run, as for a part of a split run). With bf16
+    // tiles (16 warps per SM in the update, a longer tail) two parts pay; with fp32
+    // tiles the second search launch's per-CTA set-up costs more than the overlap gains
+    // (measured at n = 64, 16 x 640 particles), so fp32 populations run as one part.
+    s->nsplit = (m >= 2 && params->v_storage == PSO_V_BF16) ? kMaxSplit : 1;
     sv.ord_resets = kOrdBuckets * (1 + s->nsplit);
     StateView h_pview[kMaxSplit] = {};
     LsArgs h_pls[kMaxSplit] = {};

@@ -107,7 +107,7 @@ class ClockSampler:
 # DRAM bytes (read + write) of one launch of each kernel on this workload, from one
 # ncu capture of each (dram__bytes_read.sum + dram__bytes_write.sum); set to None
 # when the kernel changes
-PROFILED_TRAFFIC = {"cost_ls": 865792, "update": 277613056}
+PROFILED_TRAFFIC = {"cost_ls": 865280, "update": 277471232}
 STEADY_FROM = 200      # the steady window starts after this many iterations
 FULL_ITERS = 300       # iterations of the whole configuration
 QUALITY_SEEDS = 8      # seeds of the fp32 / bf16 whole runs

@@ -113,7 +113,7 @@ __global__ void k_init(StateView s) {
 // largest value the scan saw below the maximum as an upper bound of the remaining
 // rows (count 0) and is rescanned only when that bound could matter; +inf means never
 // scanned, -inf means no rows left. Deleted rows are bits of `dead` (shared memory,
-// one word per 32 rows). The scan reads 32 rows at a time with independent loads.
+// one word per 32 rows).
 struct ColMax {
     float v;
     int cnt;

@@ -385,7 +385,9 @@ def run_e2e(args, Q, W, torch, dist, rank, world):
 
 def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src):
     if True:
-        r = results["fp32"]
+        # the fp32 population is the headline; a bf16-only run (--variants bf16) reports bf16
+        head = "fp32" if "fp32" in results else "bf16"
+        r = results[head]
         km = r["kernel_ms"]
         roofs = {
             "cost_ls": {"kernel": "k_ls_team (goal function + swap local search)", "bound": "alu",
@@ -398,17 +400,18 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src
                                     "the swapped positions and 7 per other pair"},
             "update": {"kernel": "k_update (Eq. 4 + S_v, Eq. 5 with SecondTarget, Algorithm 1)",
                        "bound": "hbm", "achieved": r["upd_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                       "frac": r["upd_gbs"] / hbm_peak, "traffic": PROFILED_TRAFFIC["update"],
+                       "frac": r["upd_gbs"] / hbm_peak,
+                       "traffic": PROFILED_TRAFFIC["update"] if head == "fp32" else None,
                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                       "bytes": "V read and written once (2 n^2 x 4 B), X and P^L read, S_x result "
-                                "written (3 n B) per particle, P^G once per swarm"},
+                       "bytes": "V read and written once (2 n^2 x %d B), X and P^L read, S_x result "
+                                "written (3 n B) per particle, P^G once per swarm" % (4 if head == "fp32" else 2)},
         }
         roof = roofs[max(roofs, key=lambda k: km[k])]  # the kernel that takes longest
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config("fp32"),
+            "data": "synthetic", "config": workload_config(head),
             "delta_evals_per_s": r["delta_evals_per_s"],
             "delta_full_per_s": r["delta_full_per_s"], "delta_incr_per_s": r["delta_incr_per_s"],
             "kernel_ms_per_step": r["kernel_ms"],
@@ -419,10 +422,12 @@ def result_line(args, results, e2e, cpu, world, hbm_peak, alu_peak_tops, alu_src
                                if r.get("search_kernels") else None),
             "bf16": ({k: results["bf16"][k] for k in ("value", "ms_per_step", "delta_evals_per_s",
                                                        "kernel_ms", "upd_gbs", "best_cost", "steady")}
-                     if "bf16" in results else None),
+                     if head == "fp32" and "bf16" in results else None),
             "moves_per_particle_iteration": r["moves_per_pit"],
             "steady": r["steady"],
-            "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": r["clocks"],
+            # kernels per iteration: update, search, bests; bf16 populations run the update
+            # and the search in two parts of whole swarms (two launches each)
+            "e2e": e2e, "gpu_launches": (3 if head == "fp32" else 5) * args.steps, "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
         return line
